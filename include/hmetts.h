@@ -1,0 +1,194 @@
+/*
+ * hmetts.h -- C ABI of the GB300 (sm_103a) hybrid purification-METTS sampler.
+ *
+ * One Markov step of the hybrid METTS-ancilla method of Chen & Stoudenmire,
+ * arXiv:1910.09142, Sec. I.C.1 ("Markov Chain Sampling Algorithm"):
+ *   1. initial state |i_n>_E |B>_C: environment sites in a product state,
+ *      cluster physical sites each in a Bell pair with an ancilla (Sec. I.C);
+ *   2. imaginary-time evolution by beta/2 of the physical legs with
+ *      second-order Trotter gates on an MPS, each two-site update split by a
+ *      truncated SVD (Sec. I.A, Sec. II "sources of error");
+ *   3. cluster observables <<A>>_n = <psi|A|psi> (Sec. I.C.1 step 3, Sec. II.A);
+ *   4. projective collapse of the environment and reset of the cluster to Bell
+ *      pairs (Sec. I.C.1 step 4, Eq. detailbalance1).
+ * The model is the S=1 Heisenberg two-leg ladder of Sec. II, Eq. H.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: HM_OK (0) or a negative HM_ERR_* code; hm_last_error()
+ *   gives a one-line message.  A failed call leaves no partially initialised
+ *   chain behind.
+ * - Memory: the caller hands one device buffer to hm_create(); the library
+ *   sub-allocates every chain and workspace inside it and never calls
+ *   cudaMalloc itself.  Host pointers passed in are owned by the caller and
+ *   only need to stay valid until the call returns.
+ * - Streams: all device work of a context is issued on the CUDA stream given
+ *   to hm_create() (NULL = legacy default stream).  Calls that return host
+ *   data synchronise that stream before returning; the others are
+ *   asynchronous.  One context must not be used from two host threads at once.
+ * - Data layout: an MPS site tensor A[k] has shape (chi_{k-1}, 3, chi_k),
+ *   row-major FP64, local basis m = +1, 0, -1.  Bond dims live on the device.
+ * - Precision: HM_FP64 runs every step in IEEE binary64.
+ */
+#ifndef HMETTS_H
+#define HMETTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HM_OK 0
+#define HM_ERR_ARG (-1)      /* invalid argument or handle                         */
+#define HM_ERR_NOMEM (-2)    /* arena cannot hold the chain (admission refused)    */
+#define HM_ERR_CUDA (-3)     /* a CUDA runtime call failed                         */
+#define HM_ERR_NUMERIC (-4)  /* SVD not converged, non-finite value, p_total <= 0  */
+#define HM_ERR_TIMEOUT (-5)  /* a device-side iteration budget ran out             */
+#define HM_ERR_STATE (-6)    /* call out of order (e.g. evolve twice, no collapse) */
+
+#define HM_FP64 0            /* every step in binary64                              */
+
+#define HM_ZX_ALTERNATE 0    /* collapse sample n in the Sz basis (n even) or Sx basis (n odd) */
+#define HM_Z_ONLY 1          /* collapse every sample in the Sz basis              */
+
+typedef struct hm_ctx hm_ctx;
+typedef int64_t hm_chain;
+
+/*
+ * Parameters of one Markov chain (Sec. II, Eq. H; Sec. I.A; Sec. I.C).
+ *   Lx            ladder length (columns); 2*Lx physical spin-1 sites, Lx >= 1.
+ *   two_W         cluster physical sites (even, 0..2*Lx): the central
+ *                 two_W/2 columns, x0 = floor((Lx - two_W/2)/2).  0 = METTS,
+ *                 2*Lx = ancilla (purification) method.
+ *   J_leg, J_rung couplings J and J_perp of Eq. H.
+ *   beta, tau     inverse temperature and Trotter step; M = round(beta/(2 tau))
+ *                 steps of size beta/(2M) are taken (Sec. I.A).
+ *   chi_max       bond dimension cap of every truncated SVD (>= 1).
+ *   cutoff        truncation error target: the smallest kept count whose
+ *                 discarded weight sum s^2 / total s^2 <= cutoff (Sec. II).
+ *   precision     HM_FP64.
+ *   seed          Philox4x32-10 key word 0 (low 32 bits) and counter word 2
+ *                 (high 32 bits).
+ *   chain_id      Philox key word 1: independent random stream per chain.
+ *   basis_schedule HM_ZX_ALTERNATE or HM_Z_ONLY.
+ *   meas_col_lo/hi measured columns [lo, hi); -1/-1 = the cluster (or the
+ *                 whole ladder when two_W = 0).  Every rung and leg bond with
+ *                 both ends inside is measured.
+ */
+typedef struct {
+  int32_t Lx, two_W;
+  double J_leg, J_rung, beta, tau;
+  int32_t chi_max;
+  double cutoff;
+  int32_t precision;
+  uint64_t seed;
+  uint32_t chain_id;
+  int32_t basis_schedule;
+  int32_t meas_col_lo, meas_col_hi;
+} hm_params;
+
+/* Create a context on CUDA device `device`, sub-allocating from the caller's
+ * device buffer [dev_mem, dev_mem + bytes) (256-byte aligned, owned by the
+ * caller, must outlive the context).  `cuda_stream` is a cudaStream_t or NULL. */
+int hm_create(hm_ctx** out, int device, void* dev_mem, size_t bytes, void* cuda_stream);
+
+/* Destroy a context (synchronises its stream).  The device buffer is not freed. */
+int hm_destroy(hm_ctx* ctx);
+
+/* Upper bound of the arena bytes one chain with these parameters needs
+ * (site tensors at their maximal bond dims, SVD and contraction workspaces).
+ * Used for admission: hm_init_chain fails with HM_ERR_NOMEM, without side
+ * effects, when the arena has fewer free bytes. */
+int hm_query_memory(const hm_params* p, size_t* bytes_out);
+
+/* Number of observables hm_measure_cluster writes per chain:
+ * 1 + 2 * (measured bonds).  Layout: [0] E_est = sum_b J_b <S_i.S_j>_b,
+ * then per measured bond b (bonds sorted by MPS index): <S_i.S_j>, <Sz_i Sz_j>. */
+int hm_num_obs(const hm_params* p, int32_t* n_obs);
+
+/* Number of environment sites (collapse outcomes per sample). */
+int hm_num_env(const hm_params* p, int32_t* n_env);
+
+/* Allocate a chain and write its first initial state (step 1).  env_init:
+ * host array of n_env outcomes in {0,1,2} (Sz basis: m = +1, 0, -1), or NULL
+ * to draw them from the chain's Philox stream with sample index n = -1. */
+int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_chain* out);
+
+/* Release a chain's arena memory (synchronises the stream). */
+int hm_free_chain(hm_ctx* ctx, hm_chain chain);
+
+/* Step 2 for n chains: evolve each chain's initial state by beta/2 with the
+ * second-order Trotter schedule; leaves the orthogonality centre on site 0.
+ * Asynchronous.  Requires the chain to be in its initial state. */
+int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n);
+
+/* Step 3: n_obs observables per chain into the HOST array out[n * n_obs]
+ * (row i = chain ids[i]).  Synchronises.  Requires an evolved chain. */
+int hm_measure_cluster(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out, int32_t n_obs);
+
+/* Step 3, device variant: out is a DEVICE array of n * n_obs doubles.
+ * Asynchronous. */
+int hm_measure_cluster_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out_dev,
+                              int32_t n_obs);
+
+/* Step 4: collapse the environment of n evolved chains, left to right, in the
+ * basis of their sample index, then reset each chain to the new initial state
+ * |i_{n+1}>_E |B>_C.  env_out (HOST, n * n_env, nullable): basis indices of
+ * the outcomes; logp_out (HOST, n, nullable): log-probability of the drawn
+ * outcome string.  Synchronises when an output pointer is given. */
+int hm_collapse(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, double* logp_out);
+
+/* Step 4, device variant: env_out_dev (int8, n * n_env) and logp_out_dev
+ * (double, n) are DEVICE arrays or NULL.  Asynchronous. */
+int hm_collapse_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out_dev,
+                       double* logp_out_dev);
+
+/* Per-chain counters since init, to HOST out[8]:
+ * [0] algorithmic flop count of the two-site contractions (2 chi_l 3 chi_m 3 chi_r),
+ * [1] gate flops (2 * 81 chi_l chi_r),
+ * [2] SVD flops charged at the dense count 4 m^2 n + 8 m n^2 + 9 n^3 (m >= n),
+ * [3] measurement + collapse transfer-matrix flops,
+ * [4] sum of discarded weights, [5] largest bond dimension seen,
+ * [6] Jacobi sweeps, [7] two-site splits.  Synchronises. */
+int hm_chain_stats(hm_ctx* ctx, hm_chain chain, double* out8);
+
+/* Copy the chain's current MPS to the host: dims_out[n_sites + 1] bond dims
+ * and the site tensors concatenated into buf (capacity `cap` doubles);
+ * *n_sites_out = sites, *n_doubles_out = doubles written.  Synchronises. */
+int hm_get_mps(hm_ctx* ctx, hm_chain chain, int32_t* dims_out, int32_t dims_cap,
+               double* buf, size_t cap, int32_t* n_sites_out, size_t* n_doubles_out);
+
+/* Replace the chain's MPS (dims[n_sites + 1], tensors concatenated as in
+ * hm_get_mps; the orthogonality centre must be on `centre`).  Marks the chain
+ * as "initial" (ready for hm_evolve) or, with evolved != 0, as evolved (ready
+ * for measure / collapse).  For checkpoint restore and debugging. */
+int hm_set_mps(hm_ctx* ctx, hm_chain chain, const int32_t* dims, int32_t n_sites,
+               const double* buf, size_t n_doubles, int32_t centre, int32_t evolved);
+
+/* Run an explicit list of n_ops two-site ops on one chain (debugging and
+ * kernel-level parity).  ops[4 i ..]: (site k, gate, absorb, exact) with gate
+ * index into the chain's gate table (0 = identity, 1 = SWAP, 2 + b = bond b
+ * of the sorted bond list at tau/2), absorb 0 = left (A_k <- U S), 1 = right
+ * (A_{k+1} <- S V^T), exact 1 = keep every nonzero singular value up to the
+ * old bond dim without renormalising (a centre move).  Asynchronous. */
+int hm_apply_ops(hm_ctx* ctx, hm_chain chain, const int32_t* ops, int32_t n_ops);
+
+/* The op schedule of hm_evolve (host planner; no GPU needed): writes up to
+ * `cap` ops as 4 int32 each (k, gate, absorb, exact) and *n_ops_out. */
+int hm_plan(const hm_params* p, int32_t* ops, int32_t cap, int32_t* n_ops_out);
+
+/* Gate table of a chain (no GPU needed): n_gates * 81 doubles, row index
+ * 3 a + b (output legs), column 3 s1 + s2; *n_gates_out = 2 + bonds. */
+int hm_gates(const hm_params* p, double* out, int32_t cap, int32_t* n_gates_out);
+
+/* The message of the last failed call on ctx (or of the last failed
+ * context-free call when ctx is NULL). */
+const char* hm_last_error(const hm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMETTS_H */

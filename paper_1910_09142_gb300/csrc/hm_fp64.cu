@@ -1,0 +1,769 @@
+// FP64 path of the hybrid purification-METTS sampler (arXiv:1910.09142).
+//
+// One CTA owns one Markov chain for the whole call: every two-site op of the
+// Trotter schedule, the cluster measurement and the environment collapse run
+// as a device-side loop over that chain's data.  On GB300 the binary64 pipe
+// (about 2 DFMA per clock per SM) is the bound of every step here, so the
+// design keeps all SMs busy with independent chains rather than tiling for
+// bandwidth: a batch of >= 152 chains fills the chip.
+//
+// Steps (Sec. I.C.1): evolve (step 2) = theta GEMM + 9x9 gate + one-sided
+// Jacobi SVD + truncation (Sec. II) + absorb; measure (step 3) = transfer
+// matrices with S^z / S^+ / S^- insertions (Eq. H); collapse + reset (step 4,
+// Eq. detailbalance1, Bell pairs of Sec. I.C).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+namespace {
+
+constexpr int NT = 256;          // threads per CTA
+constexpr int kMaxSweeps = 60;   // one-sided Jacobi sweep budget
+constexpr int TM = 64, TN = 64, TK = 16;
+
+struct GemmSmem {
+  double a[TK][TM + 1];
+  double b[TK][TN + 1];
+};
+
+struct Shared {
+  GemmSmem g;
+  double red[NT / 32][4];
+  double scal[8];
+  int32_t ival[8];
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of up to 3 values; result broadcast to every thread.
+__device__ void block_sum3(double& x, double& y, double& z, Shared& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  x = warp_sum(x);
+  y = warp_sum(y);
+  z = warp_sum(z);
+  __syncthreads();
+  if (lane == 0) {
+    sh.red[warp][0] = x;
+    sh.red[warp][1] = y;
+    sh.red[warp][2] = z;
+  }
+  __syncthreads();
+  double a = 0, b = 0, c = 0;
+  for (int w = 0; w < NT / 32; ++w) {
+    a += sh.red[w][0];
+    b += sh.red[w][1];
+    c += sh.red[w][2];
+  }
+  x = a;
+  y = b;
+  z = c;
+  __syncthreads();
+}
+
+// C[M x N] = alpha op(A) op(B) (+ beta C), row-major.  TA: A stored K x M.
+// TB: B stored N x K.  Whole CTA cooperates; ends with a barrier.
+template <bool TA, bool TB>
+__device__ void cta_gemm(int M, int N, int K, double alpha, const double* __restrict__ A, int lda,
+                         const double* __restrict__ B, int ldb, double beta, double* __restrict__ C,
+                         int ldc, GemmSmem& sm) {
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int i0 = 0; i0 < M; i0 += TM) {
+    for (int j0 = 0; j0 < N; j0 += TN) {
+      double acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+      for (int k0 = 0; k0 < K; k0 += TK) {
+        for (int e = tid; e < TM * TK; e += NT) {
+          int ii, kk;
+          if (TA) { ii = e % TM; kk = e / TM; } else { kk = e % TK; ii = e / TK; }
+          const int gi = i0 + ii, gk = k0 + kk;
+          double v = 0.0;
+          if (gi < M && gk < K) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+          sm.a[kk][ii] = v;
+        }
+        for (int e = tid; e < TN * TK; e += NT) {
+          int jj, kk;
+          if (TB) { kk = e % TK; jj = e / TK; } else { jj = e % TN; kk = e / TN; }
+          const int gj = j0 + jj, gk = k0 + kk;
+          double v = 0.0;
+          if (gj < N && gk < K) v = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
+          sm.b[kk][jj] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+          double a[4], b[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) a[r] = sm.a[kk][ty + 16 * r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) b[c] = sm.b[kk][tx + 16 * c];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty + 16 * r;
+        if (i >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = j0 + tx + 16 * c;
+          if (j >= N) continue;
+          double v = alpha * acc[r][c];
+          if (beta != 0.0) v += beta * C[(size_t)i * ldc + j];
+          C[(size_t)i * ldc + j] = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void set_error(const ChainDev* c, int code, int where, int32_t* ctx_err) {
+  if (threadIdx.x == 0) {
+    if (atomicCAS(c->status, 0, code) == 0) *c->err_where = where;
+    if (ctx_err) atomicCAS(ctx_err, 0, code);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Step 2: one two-site op (Sec. I.A gates, Sec. II truncated SVD).
+// ---------------------------------------------------------------------------
+
+// One-sided (Hestenes) Jacobi on the q x p column-major matrix W (q >= p),
+// accumulating the rotations in V (p x p).  Columns are paired by the
+// round-robin tournament so that each round's pairs are disjoint; each warp
+// rotates one pair at a time.  Returns sweeps used, or -1 if not converged.
+__device__ int cta_jacobi(double* __restrict__ W, int q, int p, double* __restrict__ V, Shared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = NT / 32;
+  for (int e = tid; e < p * p; e += NT) V[e] = (e % (p + 1) == 0) ? 1.0 : 0.0;
+  const double tol = sqrt((double)q) * 2.220446049250313e-16;
+  const int p2 = p + (p & 1);
+  int sweep = 0;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    if (tid == 0) sh.ival[0] = 0;
+    __syncthreads();
+    for (int r = 0; r < p2 - 1; ++r) {
+      for (int pi = warp; pi < p2 / 2; pi += nwarps) {
+        int a, b;
+        if (pi == 0) {
+          a = r;
+          b = p2 - 1;
+        } else {
+          a = (r + pi) % (p2 - 1);
+          b = (r - pi + (p2 - 1)) % (p2 - 1);
+        }
+        if (a >= p || b >= p) continue;
+        double* ca = W + (size_t)a * q;
+        double* cb = W + (size_t)b * q;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < q; i += 32) {
+          const double x = ca[i], y = cb[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != 0.0 && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          double t;
+          if (fabs(zeta) > 1e150) t = 0.5 / zeta;
+          else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int i = lane; i < q; i += 32) {
+            const double x = ca[i], y = cb[i];
+            ca[i] = cs * x - sn * y;
+            cb[i] = sn * x + cs * y;
+          }
+          double* va = V + (size_t)a * p;
+          double* vb = V + (size_t)b * p;
+          for (int i = lane; i < p; i += 32) {
+            const double x = va[i], y = vb[i];
+            va[i] = cs * x - sn * y;
+            vb[i] = sn * x + cs * y;
+          }
+          if (lane == 0) sh.ival[0] = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int rotated = sh.ival[0];
+    __syncthreads();
+    if (!rotated) break;
+  }
+  return sweep < kMaxSweeps ? sweep + 1 : -1;
+}
+
+// Truncation rule (Sec. II): smallest k >= 1 whose discarded weight
+// sum_{q>=k} s_q^2 / sum s^2 <= cutoff, then min(k, chi_max), then lowered to
+// the nearest gap s_{k} < s_{k-1} (1 - 1e-8).  Runs on thread 0.
+__device__ int truncation_rank(const double* s, int n, int chi_max, double cutoff, double* tail,
+                               double* total_out) {
+  tail[n] = 0.0;
+  for (int q = n - 1; q >= 0; --q) tail[q] = tail[q + 1] + s[q] * s[q];
+  const double total = tail[0];
+  *total_out = total;
+  int k = n;
+  for (int kk = 1; kk <= n; ++kk) {
+    if (tail[kk] <= cutoff * total) {
+      k = kk;
+      break;
+    }
+  }
+  if (k > chi_max) k = chi_max;
+  while (k > 1 && k < n && s[k] >= s[k - 1] * (1.0 - 1e-8)) --k;
+  return k;
+}
+
+__device__ void two_site_op(ChainDev* c, const OpDev op, int t, Shared& sh, int32_t* ctx_err) {
+  const int tid = threadIdx.x;
+  const int k = op.k;
+  const int chil = c->chi[k], chim = c->chi[k + 1], chir = c->chi[k + 2];
+  const int m = 3 * chil, n = 3 * chir;
+  double* Ak = c->site[k];
+  double* Ak1 = c->site[k + 1];
+  double* theta = c->theta;
+  double* W = c->W;
+  double* V = c->V;
+
+  // theta[(l s1), (s2 r)] = sum_m A_k[(l s1), m] A_{k+1}[m, (s2 r)]
+  cta_gemm<false, false>(m, n, chim, 1.0, Ak, chim, Ak1, n, 0.0, theta, n, sh.g);
+
+  // Gate on the physical legs, written column-oriented for the Jacobi:
+  // trans = 0: W (m x n col-major) = X;  trans = 1: W (n x m col-major) = X^T.
+  const bool trans = n > m;
+  const int q = trans ? n : m, p = trans ? m : n;
+  const double* G = c->gates + (size_t)op.gate * 81;
+  for (int e = tid; e < chil * chir; e += NT) {
+    const int l = e / chir, r = e % chir;
+    double th[9];
+#pragma unroll
+    for (int s1 = 0; s1 < 3; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < 3; ++s2) th[3 * s1 + s2] = theta[(size_t)(3 * l + s1) * n + s2 * chir + r];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        double x = 0.0;
+#pragma unroll
+        for (int u = 0; u < 9; ++u) x = fma(G[(3 * a + b) * 9 + u], th[u], x);
+        const int row = 3 * l + a, col = b * chir + r;
+        if (!trans) W[(size_t)col * q + row] = x;
+        else W[(size_t)row * q + col] = x;
+      }
+  }
+  __syncthreads();
+
+  const int sweeps = cta_jacobi(W, q, p, V, sh);
+  if (sweeps < 0) {
+    set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+    return;
+  }
+
+  // column norms (singular values), then rank-sort descending
+  double* sig_raw = theta;               // theta is free now
+  double* tail = theta + p;              // p + 1 doubles
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < p; j += NT / 32) {
+    const double* cj = W + (size_t)j * q;
+    double s2 = 0.0;
+    for (int i = lane; i < q; i += 32) s2 = fma(cj[i], cj[i], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) sig_raw[j] = sqrt(s2);
+  }
+  __syncthreads();
+  for (int j = tid; j < p; j += NT) {
+    const double sj = sig_raw[j];
+    int rank = 0;
+    for (int i = 0; i < p; ++i) {
+      const double si = sig_raw[i];
+      rank += (si > sj) || (si == sj && i < j);
+    }
+    c->sig[rank] = sj;
+    c->perm[rank] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double* s = c->sig;
+    double total;
+    int kk;
+    double nrm = 1.0;
+    if (!op.exact) {
+      kk = truncation_rank(s, p, c->chi_max, c->cutoff, tail, &total);
+      if (!(total > 0.0) || !isfinite(total)) kk = -1;
+      else {
+        double kept = 0.0;
+        for (int i = 0; i < kk; ++i) kept += s[i] * s[i];
+        nrm = 1.0 / sqrt(kept);
+        c->stats[ST_DISC] += tail[kk] / total;
+      }
+    } else {
+      kk = 0;
+      while (kk < p && kk < chim && s[kk] > 0.0) ++kk;
+      if (kk == 0) kk = -1;
+    }
+    sh.ival[1] = kk;
+    sh.scal[0] = nrm;
+    if (kk > 0) {
+      const double mm = (double)(m > n ? m : n), nn = (double)(m > n ? n : m);
+      c->stats[ST_K1] += 2.0 * chil * 3.0 * chim * 3.0 * chir;
+      c->stats[ST_K2] += 2.0 * 81.0 * chil * chir;
+      c->stats[ST_SVD] += 4.0 * mm * mm * nn + 8.0 * mm * nn * nn + 9.0 * nn * nn * nn;
+      c->stats[ST_SWEEPS] += sweeps;
+      c->stats[ST_SPLITS] += 1.0;
+      if (kk > c->stats[ST_MAXCHI]) c->stats[ST_MAXCHI] = kk;
+    }
+  }
+  __syncthreads();
+  const int kk = sh.ival[1];
+  const double nrm = sh.scal[0];
+  if (kk <= 0) {
+    set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+    return;
+  }
+  const bool absorb_left = op.absorb == 0;
+  // A_k[(l s), i] and A_{k+1}[i, (s r)] from the sorted singular triplets
+  for (int e = tid; e < m * kk; e += NT) {
+    const int row = e / kk, i = e % kk;
+    const int j = c->perm[i];
+    const double sg = c->sig[i];
+    double v;
+    if (!trans) {
+      const double w = W[(size_t)j * q + row];   // = U sigma
+      v = absorb_left ? w * nrm : w / sg;
+    } else {
+      const double u = V[(size_t)j * p + row];   // left vector
+      v = absorb_left ? u * sg * nrm : u;
+    }
+    Ak[e] = v;
+  }
+  for (int e = tid; e < kk * n; e += NT) {
+    const int i = e / n, col = e % n;
+    const int j = c->perm[i];
+    const double sg = c->sig[i];
+    double v;
+    if (!trans) {
+      const double u = V[(size_t)j * p + col];   // right vector
+      v = absorb_left ? u : u * sg * nrm;
+    } else {
+      const double w = W[(size_t)j * q + col];   // = V sigma
+      v = absorb_left ? w / sg : w * nrm;
+    }
+    Ak1[e] = v;
+  }
+  __syncthreads();
+  if (tid == 0) c->chi[k + 1] = kk;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) evolve_fp64_kernel(BatchArg b, OutArg o) {
+  __shared__ Shared sh;
+  ChainDev* c = b.c[blockIdx.x];
+  const OpDev* ops = b.ops_override ? b.ops_override : c->ops;
+  const int n_ops = b.ops_override ? b.n_override : c->n_ops;
+  const int t1 = b.t1 < n_ops ? b.t1 : n_ops;
+  for (int t = b.t0; t < t1; ++t) {
+    if (*(volatile int32_t*)c->status != 0) return;
+    __syncthreads();
+    two_site_op(c, ops[t], t, sh, o.ctx_err);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transfer matrices (steps 3 and 4).
+// ---------------------------------------------------------------------------
+
+// Eout[cr x cr] = sum_{s,t} O[s][t] A^{sT} Ein A^t   (O == nullptr: identity).
+// Z: cl x 3cr scratch.  Ein/Eout are row-major, bra index first.
+__device__ void cta_transfer(const double* Ein, const double* A, int cl, int cr, const double* O,
+                             double* Eout, double* Z, Shared& sh) {
+  if (threadIdx.x == 0) sh.scal[4] += 6.0 * cl * cl * cr + 6.0 * cl * cr * cr;
+  cta_gemm<false, false>(cl, 3 * cr, cl, 1.0, Ein, cl, A, 3 * cr, 0.0, Z, 3 * cr, sh.g);
+  if (O) {
+    for (int e = threadIdx.x; e < cl * cr; e += NT) {
+      const int i = e / cr, r = e % cr;
+      double* z = Z + (size_t)i * 3 * cr + r;
+      const double z0 = z[0], z1 = z[cr], z2 = z[2 * cr];
+      z[0] = O[0] * z0 + O[1] * z1 + O[2] * z2;
+      z[cr] = O[3] * z0 + O[4] * z1 + O[5] * z2;
+      z[2 * cr] = O[6] * z0 + O[7] * z1 + O[8] * z2;
+    }
+    __syncthreads();
+  }
+  cta_gemm<true, false>(cr, cr, 3 * cl, 1.0, A, cr, Z, cr, 0.0, Eout, cr, sh.g);
+}
+
+// Tr[sum_{s,t} O[s][t] A^{sT} E A^t] (right environment = identity).
+__device__ double cta_close(const double* E, const double* A, int cl, int cr, const double* O,
+                            double* Z, Shared& sh) {
+  if (threadIdx.x == 0) sh.scal[4] += 6.0 * cl * cl * cr + 2.0 * 9.0 * cl * cr;
+  cta_gemm<false, false>(cl, 3 * cr, cl, 1.0, E, cl, A, 3 * cr, 0.0, Z, 3 * cr, sh.g);
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < cl * cr; e += NT) {
+    const int i = e / cr, r = e % cr;
+    const double* z = Z + (size_t)i * 3 * cr + r;
+    const double* a = A + (size_t)i * 3 * cr + r;
+    const double z0 = z[0], z1 = z[cr], z2 = z[2 * cr];
+    acc += a[0] * (O[0] * z0 + O[1] * z1 + O[2] * z2) + a[cr] * (O[3] * z0 + O[4] * z1 + O[5] * z2) +
+           a[2 * cr] * (O[6] * z0 + O[7] * z1 + O[8] * z2);
+  }
+  double d1 = 0.0, d2 = 0.0;
+  block_sum3(acc, d1, d2, sh);
+  return acc;
+}
+
+__device__ __constant__ double kSz[9] = {1, 0, 0, 0, 0, 0, 0, 0, -1};
+// S+ = sqrt(2) (|+1><0| + |0><-1|); S- its transpose (basis m = +1, 0, -1)
+__device__ __constant__ double kSp[9] = {0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0, 0, 0};
+__device__ __constant__ double kSm[9] = {0, 0, 0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0};
+
+// Step 3 (Sec. I.C.1): <S_i.S_j> and <Sz_i Sz_j> on every measured bond.
+// Requires the centre on site 0, so every site >= 1 is right-orthonormal and
+// the right environment of any position is the identity.
+__global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) {
+  __shared__ Shared sh;
+  ChainDev* c = b.c[blockIdx.x];
+  const int tid = threadIdx.x;
+  double* out = o.obs + (size_t)blockIdx.x * o.n_obs;
+  if (*(volatile int32_t*)c->status != 0) {
+    for (int e = tid; e < o.n_obs; e += NT) out[e] = NAN;
+    return;
+  }
+  const int64_t cc = (int64_t)c->chi_cap * c->chi_cap;
+  double* Lp[2] = {c->env_ws, c->env_ws + cc};
+  double* Ep[2] = {c->env_ws + 2 * cc, c->env_ws + 3 * cc};
+  double* Z = c->env_ws + 4 * cc;
+  // <psi|psi> = |A_0|^2 when sites >= 1 are right-orthonormal
+  double nrm = 0.0, d1 = 0.0, d2 = 0.0;
+  {
+    const int sz0 = c->chi[0] * 3 * c->chi[1];
+    for (int e = tid; e < sz0; e += NT) nrm += c->site[0][e] * c->site[0][e];
+    block_sum3(nrm, d1, d2, sh);
+  }
+  if (tid == 0) {
+    Lp[0][0] = 1.0;
+    sh.scal[4] = 0.0;
+  }
+  __syncthreads();
+  int pos = 0, cur = 0;
+  double E_est = 0.0;
+  const double* ops1[3] = {kSz, kSp, kSm};
+  const double* ops2[3] = {kSz, kSm, kSp};
+  int bi = 0;
+  while (bi < c->n_meas) {
+    const int a = c->meas_i[bi];
+    int bend = bi;
+    while (bend < c->n_meas && c->meas_i[bend] == a) ++bend;
+    const int blast = c->meas_j[bend - 1];
+    while (pos < a) {
+      cta_transfer(Lp[cur], c->site[pos], c->chi[pos], c->chi[pos + 1], nullptr, Lp[cur ^ 1], Z, sh);
+      cur ^= 1;
+      ++pos;
+    }
+    double vals[3][8];   // up to 8 bonds per start site
+    for (int o1 = 0; o1 < 3; ++o1) {
+      int ec = 0;
+      cta_transfer(Lp[cur], c->site[a], c->chi[a], c->chi[a + 1], ops1[o1], Ep[ec], Z, sh);
+      for (int kk = a + 1; kk <= blast; ++kk) {
+        for (int q = bi; q < bend; ++q) {
+          if (c->meas_j[q] == kk)
+            vals[o1][q - bi] = cta_close(Ep[ec], c->site[kk], c->chi[kk], c->chi[kk + 1], ops2[o1], Z, sh);
+        }
+        if (kk < blast) {
+          cta_transfer(Ep[ec], c->site[kk], c->chi[kk], c->chi[kk + 1], nullptr, Ep[ec ^ 1], Z, sh);
+          ec ^= 1;
+        }
+      }
+    }
+    if (tid == 0) {
+      for (int q = bi; q < bend; ++q) {
+        const double zz = vals[0][q - bi] / nrm;
+        const double ss = zz + 0.5 * (vals[1][q - bi] + vals[2][q - bi]) / nrm;
+        out[1 + 2 * q] = ss;
+        out[2 + 2 * q] = zz;
+        E_est += c->meas_J[q] * ss;
+      }
+    }
+    bi = bend;
+  }
+  if (tid == 0) {
+    out[0] = E_est;
+    c->stats[ST_TRANSFER] += sh.scal[4];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Step 4: collapse and reset.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                             uint32_t k0, uint32_t k1) {
+  const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+  const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+  const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+  c0 = n0;
+  c1 = lo1;
+  c2 = n2;
+  c3 = lo0;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): counter (n, ordinal, seed_hi, 0),
+// key (seed_lo, chain_id); u = ((x0 >> 5) 2^26 + (x1 >> 6)) 2^-53.
+__device__ double philox_uniform(uint32_t n, uint32_t ordinal, uint32_t seed_hi, uint32_t seed_lo,
+                                 uint32_t chain) {
+  uint32_t c0 = n, c1 = ordinal, c2 = seed_hi, c3 = 0u;
+  uint32_t k0 = seed_lo, k1 = chain;
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    philox_round(c0, c1, c2, c3, k0, k1);
+  }
+  return ((double)(c0 >> 5) * 67108864.0 + (double)(c1 >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// First b with u < cumulative p_b, else the last b with p_b > 0.
+__device__ int choose3(const double p[3], double u) {
+  double acc = 0.0;
+  for (int b = 0; b < 3; ++b) {
+    acc += p[b];
+    if (u < acc) return b;
+  }
+  for (int b = 2; b >= 0; --b)
+    if (p[b] > 0.0) return b;
+  return -1;
+}
+
+__device__ void basis_rows(const ChainDev* c, int basis, double B[9]) {
+  for (int i = 0; i < 9; ++i) B[i] = basis ? c->xbasis[i] : ((i % 4 == 0) ? 1.0 : 0.0);
+}
+
+// Sequential projective measurement of the environment, left to right, in the
+// basis of sample n (Sec. I.C.1 step 4); cluster sites are traced out, which
+// turns the boundary vector into a density matrix (Eq. detailbalance1).
+__global__ void __launch_bounds__(NT) collapse_fp64_kernel(BatchArg b, OutArg o) {
+  __shared__ Shared sh;
+  ChainDev* c = b.c[blockIdx.x];
+  const int tid = threadIdx.x;
+  if (*(volatile int32_t*)c->status != 0) return;
+  const int n_sample = c->counters[0];
+  const int basis = (c->basis_zx && (n_sample & 1)) ? 1 : 0;
+  double B[9];
+  basis_rows(c, basis, B);
+  const int64_t cc = (int64_t)c->chi_cap * c->chi_cap;
+  double* R[2] = {c->env_ws, c->env_ws + cc};
+  double* X = c->env_ws + 2 * cc;      // cl x 3cr
+  double* At = c->env_ws + 5 * cc;     // cl x cr
+  double* Y = c->env_ws + 6 * cc;      // cl x cr
+  int cur = 0;
+  bool vec_mode = true;
+  if (tid == 0) {
+    R[0][0] = 1.0;                     // v = [1]
+    sh.scal[4] = 0.0;
+  }
+  __syncthreads();
+  int e_ord = 0;
+  double logp = 0.0;
+  for (int k = 0; k < c->n_sites; ++k) {
+    const double* A = c->site[k];
+    const int cl = c->chi[k], cr = c->chi[k + 1];
+    if (c->site_kind[k] == SITE_ENV) {
+      double q[3] = {0.0, 0.0, 0.0};
+      if (vec_mode) {
+        // X[(s r)] = sum_l v[l] A[l, s, r]
+        for (int e = tid; e < 3 * cr; e += NT) {
+          double acc = 0.0;
+          for (int l = 0; l < cl; ++l) acc = fma(R[cur][l], A[(size_t)l * 3 * cr + e], acc);
+          X[e] = acc;
+        }
+        __syncthreads();
+        for (int r = tid; r < cr; r += NT) {
+          const double x0 = X[r], x1 = X[cr + r], x2 = X[2 * cr + r];
+          for (int bb = 0; bb < 3; ++bb) {
+            const double w = B[3 * bb] * x0 + B[3 * bb + 1] * x1 + B[3 * bb + 2] * x2;
+            q[bb] = fma(w, w, q[bb]);
+          }
+        }
+      } else {
+        cta_gemm<false, false>(cl, 3 * cr, cl, 1.0, R[cur], cl, A, 3 * cr, 0.0, X, 3 * cr, sh.g);
+        for (int e = tid; e < cl * cr; e += NT) {
+          const int i = e / cr, r = e % cr;
+          const double* a = A + (size_t)i * 3 * cr + r;
+          const double* x = X + (size_t)i * 3 * cr + r;
+          const double a0 = a[0], a1 = a[cr], a2 = a[2 * cr];
+          const double x0 = x[0], x1 = x[cr], x2 = x[2 * cr];
+          for (int bb = 0; bb < 3; ++bb) {
+            const double at = B[3 * bb] * a0 + B[3 * bb + 1] * a1 + B[3 * bb + 2] * a2;
+            const double yt = B[3 * bb] * x0 + B[3 * bb + 1] * x1 + B[3 * bb + 2] * x2;
+            q[bb] = fma(at, yt, q[bb]);
+          }
+        }
+      }
+      block_sum3(q[0], q[1], q[2], sh);
+      if (tid == 0) {
+        const double tot = q[0] + q[1] + q[2];
+        int pick = -1;
+        double pb = 0.0;
+        if (tot > 0.0 && isfinite(tot)) {
+          const double p[3] = {q[0] / tot, q[1] / tot, q[2] / tot};
+          const double u = philox_uniform((uint32_t)n_sample, (uint32_t)e_ord, c->seed_hi, c->seed_lo,
+                                          c->chain_id);
+          pick = choose3(p, u);
+          if (pick >= 0) pb = p[pick];
+        }
+        sh.ival[2] = pick;
+        sh.scal[1] = pick >= 0 ? q[pick] : 0.0;
+        if (pick >= 0) logp += log(pb);
+      }
+      __syncthreads();
+      const int pick = sh.ival[2];
+      const double qb = sh.scal[1];
+      if (pick < 0) {
+        set_error(c, HM_ERR_NUMERIC, 100000 + k, o.ctx_err);
+        return;
+      }
+      if (tid == 0) {
+        c->env_out[e_ord] = pick;
+        if (o.env) o.env[(size_t)blockIdx.x * o.n_env + e_ord] = (int8_t)pick;
+      }
+      const double b0 = B[3 * pick], b1 = B[3 * pick + 1], b2 = B[3 * pick + 2];
+      if (vec_mode) {
+        const double sc = 1.0 / sqrt(qb);
+        for (int r = tid; r < cr; r += NT)
+          R[cur ^ 1][r] = (b0 * X[r] + b1 * X[cr + r] + b2 * X[2 * cr + r]) * sc;
+        __syncthreads();
+      } else {
+        for (int e = tid; e < cl * cr; e += NT) {
+          const int i = e / cr, r = e % cr;
+          const double* a = A + (size_t)i * 3 * cr + r;
+          const double* x = X + (size_t)i * 3 * cr + r;
+          At[e] = b0 * a[0] + b1 * a[cr] + b2 * a[2 * cr];
+          Y[e] = b0 * x[0] + b1 * x[cr] + b2 * x[2 * cr];
+        }
+        __syncthreads();
+        cta_gemm<true, false>(cr, cr, cl, 1.0 / qb, At, cr, Y, cr, 0.0, R[cur ^ 1], cr, sh.g);
+        if (tid == 0) sh.scal[4] += 6.0 * cl * cl * cr + 2.0 * cl * cr * cr;
+      }
+      cur ^= 1;
+      ++e_ord;
+    } else {
+      if (vec_mode) {
+        // rho = v v^T
+        for (int e = tid; e < cl * cl; e += NT) R[cur ^ 1][e] = R[cur][e / cl] * R[cur][e % cl];
+        __syncthreads();
+        cur ^= 1;
+        vec_mode = false;
+      }
+      cta_transfer(R[cur], A, cl, cr, nullptr, R[cur ^ 1], X, sh);
+      cur ^= 1;
+    }
+  }
+  if (tid == 0) {
+    if (o.logp) o.logp[blockIdx.x] = logp;
+    c->counters[0] = n_sample + 1;
+    c->counters[1] = basis;
+    c->stats[ST_TRANSFER] += sh.scal[4];
+  }
+}
+
+// Writes the initial state |i>_E |B>_C from env_out and counters[1]
+// (Sec. I.C.1 step 1): environment sites (1,3,1) basis vectors, cluster
+// physical sites delta(s,a)/sqrt(3) of shape (1,3,3), ancillas delta(a,s) of
+// shape (3,3,1).  With draw_initial, first draws the environment in the Sz
+// basis with p = 1/3 each and sample index n = -1.
+__global__ void __launch_bounds__(NT) reset_kernel(BatchArg b, OutArg o, int draw_initial) {
+  ChainDev* c = b.c[blockIdx.x];
+  const int tid = threadIdx.x;
+  if (*(volatile int32_t*)c->status != 0) return;
+  if (draw_initial) {
+    const double third = 1.0 / 3.0;
+    const double p[3] = {third, third, third};
+    for (int e = tid; e < c->n_env; e += NT) {
+      const double u = philox_uniform(0xFFFFFFFFu, (uint32_t)e, c->seed_hi, c->seed_lo, c->chain_id);
+      c->env_out[e] = choose3(p, u);
+    }
+    if (tid == 0) {
+      c->counters[0] = 0;
+      c->counters[1] = 0;
+    }
+    __syncthreads();
+  }
+  const int basis = c->counters[1];
+  double B[9];
+  basis_rows(c, basis, B);
+  const double r3 = 1.0 / sqrt(3.0);
+  // env ordinal of site k = number of env sites before k
+  for (int k = tid; k < c->n_sites; k += NT) {
+    double* A = c->site[k];
+    const int kind = c->site_kind[k];
+    if (kind == SITE_ENV) {
+      int ord = 0;
+      for (int s = 0; s < k; ++s) ord += c->site_kind[s] == SITE_ENV;
+      const int pick = c->env_out[ord];
+      for (int s = 0; s < 3; ++s) A[s] = B[3 * pick + s];
+    } else if (kind == SITE_CPHYS) {
+      for (int e = 0; e < 9; ++e) A[e] = (e % 4 == 0) ? r3 : 0.0;
+    } else {
+      for (int e = 0; e < 9; ++e) A[e] = (e % 4 == 0) ? 1.0 : 0.0;
+    }
+  }
+  for (int i = tid; i <= c->n_sites; i += NT)
+    c->chi[i] = (i > 0 && i < c->n_sites && c->site_kind[i - 1] == SITE_CPHYS) ? 3 : 1;
+}
+
+}  // namespace
+
+static int check_launch() {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int launch_evolve_fp64(const BatchArg& b, const OutArg& o, void* stream) {
+  if (b.n <= 0) return HM_OK;
+  evolve_fp64_kernel<<<b.n, NT, 0, (cudaStream_t)stream>>>(b, o);
+  return check_launch();
+}
+
+int launch_measure_fp64(const BatchArg& b, const OutArg& o, void* stream) {
+  if (b.n <= 0) return HM_OK;
+  measure_fp64_kernel<<<b.n, NT, 0, (cudaStream_t)stream>>>(b, o);
+  return check_launch();
+}
+
+int launch_collapse_fp64(const BatchArg& b, const OutArg& o, void* stream) {
+  if (b.n <= 0) return HM_OK;
+  collapse_fp64_kernel<<<b.n, NT, 0, (cudaStream_t)stream>>>(b, o);
+  const int rc = check_launch();
+  if (rc != HM_OK) return rc;
+  reset_kernel<<<b.n, NT, 0, (cudaStream_t)stream>>>(b, o, 0);
+  return check_launch();
+}
+
+int launch_reset(const BatchArg& b, const OutArg& o, int draw_initial, void* stream) {
+  if (b.n <= 0) return HM_OK;
+  reset_kernel<<<b.n, NT, 0, (cudaStream_t)stream>>>(b, o, draw_initial);
+  return check_launch();
+}
+
+}  // namespace hm

@@ -1,0 +1,88 @@
+// Internal data structures shared by the host API (hm_api.cu) and the FP64
+// kernels (hm_fp64.cu).  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/hmetts.h"
+
+namespace hm {
+
+// Site kinds of the hybrid state (Sec. I.C, Fig. 4).
+enum : int32_t { SITE_ENV = 0, SITE_CPHYS = 1, SITE_ANC = 2 };
+
+// Gate table layout of the CUDA side: 0 identity, 1 SWAP, 2 + b bond b.
+enum : int32_t { GATE_ID = 0, GATE_SWAP = 1, GATE_BOND0 = 2 };
+
+// One two-site op: theta = A_k A_{k+1}, gate, SVD, truncate, absorb.
+struct OpDev {
+  int32_t k;       // left site of the pair
+  int32_t gate;    // gate table index
+  int32_t absorb;  // 0: A_k <- U S (centre k), 1: A_{k+1} <- S V^T (centre k+1)
+  int32_t exact;   // 1: centre move (keep all nonzero s up to the old bond, no renorm)
+};
+
+// Per-chain statistics slots (doubles), see hm_chain_stats.
+enum : int { ST_K1 = 0, ST_K2, ST_SVD, ST_TRANSFER, ST_DISC, ST_MAXCHI, ST_SWEEPS, ST_SPLITS, ST_N };
+
+// Device-resident description and state of one chain.  Lives in the arena;
+// every pointer is a device address inside the same chain block.
+struct ChainDev {
+  // static description
+  int32_t n_sites, n_ops, chi_max, n_env, n_meas, n_gates;
+  int32_t basis_zx, first_cluster;
+  uint32_t seed_lo, seed_hi, chain_id, pad0;
+  double cutoff;
+  const OpDev* ops;          // n_ops
+  const double* gates;       // n_gates * 81, row (3a+b), column (3 s1 + s2)
+  const int32_t* site_kind;  // n_sites
+  const int32_t* meas_i;     // n_meas, sorted by (i, j)
+  const int32_t* meas_j;
+  const double* meas_J;
+  const double* xbasis;      // 9: rows are the Sx eigenvectors (m=+1,0,-1 order)
+  // mutable state
+  double** site;             // n_sites device pointers (fixed slots)
+  int32_t* chi;              // n_sites + 1 bond dims; site s is (chi[s], 3, chi[s+1])
+  int32_t* env_out;          // n_env: basis index of the current environment state
+  int32_t* counters;         // [0] sample index n, [1] basis of the current initial state
+  double* stats;             // ST_N
+  int32_t* status;           // 0 = ok, else a negative HM_ERR_* code
+  int32_t* err_where;        // op index / site where the error happened
+  // workspaces
+  double* theta;             // ws_cap doubles: two-site tensor, then scratch
+  double* W;                 // ws_cap: the matrix the one-sided Jacobi orthogonalises
+  double* V;                 // ws_cap: accumulated rotations
+  double* sig;               // sv_cap: sorted singular values
+  int32_t* perm;             // sv_cap: sorted index -> Jacobi column
+  double* env_ws;            // env_cap: transfer-matrix workspace (measure, collapse)
+  int64_t ws_cap, env_cap;
+  int32_t sv_cap, chi_cap;
+};
+
+constexpr int kMaxBatch = 448;   // chains per launch (kernel parameter block < 4 KB)
+
+struct BatchArg {
+  int32_t n;
+  int32_t t0, t1;                // op range [t0, t1) for the evolve kernel
+  int32_t n_override;            // op count of ops_override
+  const OpDev* ops_override;     // explicit op list (debug / kernel parity) or nullptr
+  ChainDev* c[kMaxBatch];
+};
+
+struct OutArg {
+  double* obs;        // device, n * n_obs (measure) or nullptr
+  int32_t n_obs;
+  int32_t n_env;      // stride of env_out
+  int8_t* env;        // device, n * n_env (collapse) or nullptr
+  double* logp;       // device, n (collapse) or nullptr
+  int32_t* ctx_err;   // device error word shared by the context
+};
+
+// Kernel launchers (hm_fp64.cu).
+int launch_evolve_fp64(const BatchArg& b, const OutArg& o, void* stream);
+int launch_measure_fp64(const BatchArg& b, const OutArg& o, void* stream);
+int launch_collapse_fp64(const BatchArg& b, const OutArg& o, void* stream);
+int launch_reset(const BatchArg& b, const OutArg& o, int draw_initial, void* stream);
+
+}  // namespace hm

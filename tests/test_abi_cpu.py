@@ -1,0 +1,107 @@
+"""The C-ABI library: build, exported symbols and its host-side logic (no GPU).
+
+The host planner and gate table of the CUDA library are independent
+implementations of the same schedule the oracle follows; here they are
+compared op by op and entry by entry, through the C ABI.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import model
+from paper_1910_09142_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(build.LIB):
+        build.build()
+    return binding.load()
+
+
+def _header_symbols():
+    text = open(os.path.join(ROOT, "include", "hmetts.h")).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(hm_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = _header_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(binding.EXPORTS) == syms
+
+
+CASES = [(16, 8), (4, 4), (1, 2), (3, 0), (2, 4), (5, 2), (6, 12)]
+
+
+def _oracle_ops_as_abi(lad, n_steps):
+    """Oracle op list in the CUDA op encoding (k, gate, absorb, exact)."""
+    out = []
+    for kind, k, g, absorb in model.plan_ops(lad, n_steps):
+        if kind == model.SPLIT:
+            gate = 1 if g == model.GATE_SWAP else 2 + (g - 1)
+            out.append((k, gate, absorb, 0))
+        elif kind == model.MOVE_R:
+            out.append((k, 0, 1, 1))
+        else:
+            out.append((k - 1, 0, 0, 1))
+    return np.array(out, dtype=np.int32).reshape(-1, 4)
+
+
+@pytest.mark.parametrize("Lx,two_W", CASES)
+def test_planner_matches_oracle(lib, Lx, two_W):
+    beta, tau = 0.6, 0.1
+    p = binding.params(Lx, two_W, beta=beta, tau=tau)
+    lad = model.Ladder(Lx, two_W)
+    n_steps, _ = model.trotter_steps(beta, tau)
+    assert np.array_equal(binding.plan(p), _oracle_ops_as_abi(lad, n_steps))
+
+
+def test_planner_beta_zero_is_empty(lib):
+    assert len(binding.plan(binding.params(4, 4, beta=0.0))) == 0
+
+
+@pytest.mark.parametrize("Jl,Jr,tau", [(1.0, 1.0, 0.1), (0.7, 0.5, 0.05), (1.0, 0.0, 0.2)])
+def test_gate_table_matches_oracle(lib, Jl, Jr, tau):
+    p = binding.params(3, 2, J_leg=Jl, J_rung=Jr, beta=1.0, tau=tau)
+    lad = model.Ladder(3, 2, Jl, Jr)
+    _, teff = model.trotter_steps(1.0, tau)
+    og = model.gate_table(lad, teff)
+    cg = binding.gates(p)
+    assert len(cg) == len(og) + 1
+    assert np.array_equal(cg[0], np.eye(9))
+    assert np.array_equal(cg[1], og[0])                       # SWAP
+    for b in range(len(lad.bonds)):
+        assert np.abs(cg[2 + b] - og[1 + b]).max() < 2e-15
+
+
+@pytest.mark.parametrize("Lx,two_W,cols", [(16, 8, None), (4, 4, None), (4, 0, None), (5, 2, (0, 5)), (3, 6, (1, 2))])
+def test_observable_and_env_counts(lib, Lx, two_W, cols):
+    p = binding.params(Lx, two_W, meas_cols=cols)
+    lad = model.Ladder(Lx, two_W)
+    mb = lad.measured_bonds() if cols is None else lad.measured_bonds(*cols)
+    assert binding.num_obs(p) == 1 + 2 * len(mb)
+    assert binding.num_env(p) == len(lad.env)
+
+
+def test_memory_query_scales_with_chi(lib):
+    small = binding.query_memory(binding.params(16, 8, chi_max=64))
+    big = binding.query_memory(binding.params(16, 8, chi_max=256))
+    assert 0 < small < big
+    # site tensors alone at the full bond caps: 40 sites x 3 x 256^2 doubles
+    assert big > 40 * 3 * 256 * 256 * 8 * 0.5
+
+
+@pytest.mark.parametrize("kw", [dict(Lx=0, two_W=0), dict(Lx=4, two_W=3), dict(Lx=4, two_W=10),
+                                dict(Lx=4, two_W=4, tau=0.0), dict(Lx=4, two_W=4, chi_max=0),
+                                dict(Lx=4, two_W=4, cutoff=1.5), dict(Lx=4, two_W=4, beta=-1.0),
+                                dict(Lx=4, two_W=4, meas_cols=(3, 2))])
+def test_invalid_parameters_rejected(lib, kw):
+    with pytest.raises(binding.HmError) as e:
+        binding.num_obs(binding.params(**kw))
+    assert e.value.code == binding.HM_ERR_ARG

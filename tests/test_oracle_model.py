@@ -113,3 +113,4 @@ def test_trotter_steps():
     assert model.trotter_steps(0.0, 0.1)[0] == 0
     m, t = model.trotter_steps(1.0, 0.3)
     assert m == 2 and abs(t - 0.25) < 1e-15
+    assert model.trotter_steps(1.0, 0.2)[0] == 3      # 2.5 rounds up
