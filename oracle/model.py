@@ -29,6 +29,8 @@ implement exactly these, independently):
   moves cover any remaining distance; after the last gate the centre is moved
   to site 0.
 """
+import math
+
 import numpy as np
 
 D = 3  # spin-1 local dimension (Sec. I.A)
@@ -137,12 +139,15 @@ class Ladder:
 
 
 def trotter_steps(beta, tau):
-    """Number of steps M and the step tau_eff = beta/(2M) (Sec. I.A)."""
+    """Number of steps M and the step tau_eff = beta/(2M) (Sec. I.A).
+
+    M = floor(beta/(2 tau) + 1/2) (halves round up), at least 1 for beta > 0.
+    """
     if beta < 0 or tau <= 0:
         raise ValueError("beta >= 0 and tau > 0 required")
     if beta == 0:
         return 0, tau
-    m = max(1, int(round(beta / (2.0 * tau))))
+    m = max(1, int(math.floor(beta / (2.0 * tau) + 0.5)))
     return m, beta / (2.0 * m)
 
 
