@@ -1,0 +1,260 @@
+"""Benchmark: hybrid-METTS samples/s on GB300 (Lx=16 ladder, chi=256).
+
+One step = one Markov step (evolve by beta/2, measure the cluster, collapse
+the environment and reset) of every chain of the batch.  Workload: S=1
+Heisenberg ladder Lx=16 (32 spins), J_leg = J_rung = 1, 2W = 8 cluster
+sites, beta = 1, tau = 0.05 (M = 10), chi_max = 256, truncation cutoff 1e-7,
+256 independent chains per GPU in one batched launch; synthetic (the model
+is Hamiltonian-defined), seeds (0, chain id).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Prints one JSON line on rank 0.  For N > 1 run under torchrun: each rank
+owns its own chains (weak scaling, no data exchange); only the timing
+barrier and the max-over-ranks reduction cross ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9      # 152 SMs x 128 FP32 lanes x FMA x max SM clock
+FP64_ALU_PEAK = 1.25e12                      # nominal GB300 binary64 rate
+METRIC = "hybrid-METTS samples/s (Lx=16 ladder, chi=256)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--chains", type=int, default=256)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, chains):
+    cfg = synth.ladder("ladder16")
+    return {"workload": "S=1 Heisenberg ladder Lx=16 x 2, 2W=8 cluster sites, beta=1, tau=0.05, "
+                        "chi_max=256, cutoff=1e-7, %d chains/GPU" % chains,
+            "Lx": cfg["Lx"], "two_W": cfg["two_W"], "beta": cfg["beta"], "tau": cfg["tau"],
+            "chi_max": cfg["chi_max"], "cutoff": cfg["cutoff"], "J_leg": cfg["J_leg"],
+            "J_rung": cfg["J_rung"], "chains_per_gpu": chains, "precision": args.precision,
+            "l2": "inputs larger than L2 (chain states ~%.0f GB resident)" % (chains * 0.075),
+            "parallelism": "independent chains per GPU" if args.gpus > 1 else "1 GPU"}
+
+
+def oracle_sample_rate(n_samples=1):
+    """The FP64 oracle as it stands: n_samples Markov steps of chain 0, 1 core."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle.chain import HybridChain
+    cfg = synth.ladder("ladder16")
+    ch = HybridChain(seed=0, chain_id=0, **cfg)
+    t0 = time.perf_counter()
+    for _ in range(n_samples):
+        ch.sample()
+    dt = time.perf_counter() - t0
+    return n_samples / dt, dt
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 8 for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample_rate(1)
+    rates = [oracle_sample_rate(1)[0] for _ in range(args.steps)]
+    total_t = sum(1.0 / r for r in rates)
+    value = args.steps / total_t
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": dict(workload_config(args, args.chains), precision="fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": "one Markov step of chain 0 per timed step (numpy/LAPACK FP64, 1 thread)"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1910_09142_gb300 import binding, build
+    if not os.path.exists(build.LIB):
+        build.build()
+    b = binding
+    cfg = synth.ladder("ladder16")
+    prec = b.HM_MIXED if args.precision == "mixed" else b.HM_FP64
+    n = args.chains
+    ps = [b.params(**cfg, precision=prec, seed=0, chain_id=rank * n + i) for i in range(n)]
+    per = b.query_memory(ps[0])
+    stream = torch.cuda.Stream(local)
+    ctx = b.Context(per * n + (512 << 20), device=local, stream=stream)
+    ids = [ctx.init_chain(p) for p in ps]
+    n_obs, n_env = b.num_obs(ps[0]), b.num_env(ps[0])
+    obs = torch.empty((n, n_obs), dtype=torch.float64, device="cuda:%d" % local)
+    env = torch.empty((n, n_env), dtype=torch.int8, device="cuda:%d" % local)
+    logp = torch.empty((n,), dtype=torch.float64, device="cuda:%d" % local)
+    max_ops = len(b.plan(ps[0]))
+    batches = (n + 447) // 448
+    launches_per_step = batches * ((max_ops + 4095) // 4096 + 3)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+
+    def step(i=None):
+        if i is not None:
+            ev[2 + 2 * i].record(stream)
+        ctx.evolve(ids)
+        if i is not None:
+            ev[3 + 2 * i].record(stream)
+        ctx.measure_device(ids, obs)
+        ctx.collapse_device(ids, env, logp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats0 = np.array([ctx.stats(c) for c in ids])
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    step_ev[0].record(stream)
+    for i in range(args.steps):
+        step(i)
+        step_ev[i + 1].record(stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_ms = ev[0].elapsed_time(ev[1])
+    evolve_ms = [ev[2 + 2 * i].elapsed_time(ev[3 + 2 * i]) for i in range(args.steps)]
+    lat = [step_ev[i].elapsed_time(step_ev[i + 1]) for i in range(args.steps)]
+    stats1 = np.array([ctx.stats(c) for c in ids])
+    d = stats1 - stats0
+    flops_alg = float(d[:, 0].sum() + d[:, 1].sum() + d[:, 2].sum())
+    if world > 1:
+        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda:%d" % local)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * n * args.steps / (t_ms / 1e3)
+
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.evolve(ids)
+            ctx.measure(ids, n_obs)            # host output (D2H inside)
+            ctx.collapse(ids, n_env)           # host outputs (D2H inside)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda:%d" % local)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n * args.steps / e2e_s, "unit": "samples/s",
+               "h2d_bytes_per_step": 8 * n,                      # chain handles
+               "d2h_bytes_per_step": n * (8 * n_obs + n_env + 8)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    evolve_s = sum(evolve_ms) / 1e3
+    achieved = flops_alg / evolve_s / 1e12
+    peak = FP32_ALU_PEAK / 1e12 if prec == b.HM_MIXED else FP64_ALU_PEAK / 1e12
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == b.HM_MIXED else "f64", "data": "synthetic",
+            "config": workload_config(args, n),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "note": "per-sample latency = step time (all chains of a step finish together)"},
+            "roofline": {"bound": "alu", "kernel": "evolve (two-site ops)", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_per_step": flops_alg / args.steps,
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec == b.HM_MIXED
+                         else "nominal GB300 FP64 rate"},
+            "evolve_share": sum(evolve_ms) / t_ms,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk}
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        rate, dt = oracle_sample_rate(1)
+        line["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                                "sample": "one Markov step of chain 0 (%.1f s, numpy/LAPACK FP64, 1 thread)" % dt}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -20,6 +20,7 @@ HM_ERR_NUMERIC = -4
 HM_ERR_TIMEOUT = -5
 HM_ERR_STATE = -6
 HM_FP64 = 0
+HM_MIXED = 1
 HM_ZX_ALTERNATE = 0
 HM_Z_ONLY = 1
 

@@ -60,7 +60,8 @@ int check_params(const hm_params* p, std::string* err) {
   if (!std::isfinite(p->J_leg) || !std::isfinite(p->J_rung)) return fail(err, HM_ERR_ARG, "couplings must be finite");
   if (p->chi_max < 1 || p->chi_max > 4096) return fail(err, HM_ERR_ARG, "chi_max must be in [1, 4096]");
   if (!(p->cutoff >= 0.0) || !(p->cutoff < 1.0)) return fail(err, HM_ERR_ARG, "cutoff must be in [0, 1)");
-  if (p->precision != HM_FP64) return fail(err, HM_ERR_ARG, "unsupported precision %d", p->precision);
+  if (p->precision != HM_FP64 && p->precision != HM_MIXED)
+    return fail(err, HM_ERR_ARG, "unsupported precision %d", p->precision);
   if (p->basis_schedule != HM_ZX_ALTERNATE && p->basis_schedule != HM_Z_ONLY)
     return fail(err, HM_ERR_ARG, "unknown basis schedule");
   const bool dflt = p->meas_col_lo == -1 && p->meas_col_hi == -1;
@@ -652,21 +653,30 @@ int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
   for (Chain* c : cs)
     if (c->phase != 0) return fail(&ctx->err, HM_ERR_STATE, "hm_evolve needs a chain in its initial state");
   HM_CUDA(ctx, cudaSetDevice(ctx->device));
-  int max_ops = 0;
-  for (Chain* c : cs) max_ops = std::max<int>(max_ops, (int)c->ops.size());
   OutArg o{};
   o.ctx_err = ctx->err_word;
-  rc = for_batches(cs, [&](BatchArg& b, int) {
-    const int chunk = 4096;
-    for (int t0 = 0; t0 < max_ops; t0 += chunk) {
-      b.t0 = t0;
-      b.t1 = t0 + chunk;
-      const int r = launch_evolve_fp64(b, o, ctx->stream);
-      if (r != HM_OK) return r;
-    }
-    return HM_OK;
-  });
-  if (rc != HM_OK) return fail(&ctx->err, rc, "evolve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int prec : {HM_FP64, HM_MIXED}) {
+    std::vector<Chain*> group;
+    int max_ops = 0, chi_cap = 1;
+    for (Chain* c : cs)
+      if (c->p.precision == prec) {
+        group.push_back(c);
+        max_ops = std::max<int>(max_ops, (int)c->ops.size());
+        chi_cap = std::max<int>(chi_cap, c->mp.chi_cap);
+      }
+    rc = for_batches(group, [&](BatchArg& b, int) {
+      const int chunk = 4096;
+      for (int t0 = 0; t0 < max_ops; t0 += chunk) {
+        b.t0 = t0;
+        b.t1 = t0 + chunk;
+        const int r = prec == HM_FP64 ? launch_evolve_fp64(b, o, ctx->stream)
+                                      : launch_evolve_mixed(b, o, chi_cap, ctx->stream);
+        if (r != HM_OK) return r;
+      }
+      return HM_OK;
+    });
+    if (rc != HM_OK) return fail(&ctx->err, rc, "evolve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
   for (Chain* c : cs) c->phase = 1;
   return HM_OK;
 }
@@ -865,7 +875,8 @@ int hm_apply_ops(hm_ctx* ctx, hm_chain chain, const int32_t* ops, int32_t n_ops)
   b.n_override = n_ops;
   OutArg o{};
   o.ctx_err = ctx->err_word;
-  rc = launch_evolve_fp64(b, o, ctx->stream);
+  rc = c->p.precision == HM_FP64 ? launch_evolve_fp64(b, o, ctx->stream)
+                                  : launch_evolve_mixed(b, o, c->mp.chi_cap, ctx->stream);
   if (rc != HM_OK) return fail(&ctx->err, rc, "apply_ops launch failed");
   return check_device_error(ctx);   // the scratch op list must outlive the kernel
 }

