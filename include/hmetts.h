@@ -191,6 +191,33 @@ int hm_plan(const hm_params* p, int32_t* ops, int32_t cap, int32_t* n_ops_out);
  * 3 a + b (output legs), column 3 s1 + s2; *n_gates_out = 2 + bonds. */
 int hm_gates(const hm_params* p, double* out, int32_t cap, int32_t* n_gates_out);
 
+/* ---- Allocation-free entry point -------------------------------------------
+ * The paper has no counterpart: this is a library convenience.  It serves
+ * callers that cannot call cudaMalloc (work captured into a CUDA graph, code
+ * running inside another framework's memory pool, processes whose device
+ * allocator belongs to someone else): it performs ONE two-site update of
+ * step 2 -- theta = A B, the 9x9 gate, the binary64 one-sided Jacobi SVD,
+ * the truncation rule and the absorb -- with all scratch in a fixed device
+ * array of the library (about 4.3 MB, kept by every GPU that loads the
+ * library until the process exits).  It never allocates or frees memory.
+ *   A_dev     (chi_l, 3, chi_m) binary64, device; B_dev (chi_m, 3, chi_r).
+ *   gate_dev  81 binary64 on the device, row 3a+b, column 3 s1 + s2.
+ *   chi_l, chi_m, chi_r, chi_max must lie in [1, 128]; larger values return
+ *             HM_ERR_ARG (the fixed scratch cannot hold them).
+ *   A_out_dev (chi_l, 3, k) and B_out_dev (k, 3, chi_r) with room for
+ *             k = min(3 chi_l, 3 chi_r, chi_max); k_out_dev: one int32 that
+ *             receives k, or a negative HM_ERR_* code if the SVD failed.
+ *   absorb    0: A_out = U S (centre left), 1: B_out = S V^T (centre right).
+ * Asynchronous on cuda_stream.  The first call on each device looks up the
+ * device address of the scratch array (set-up; make that first call before
+ * any stream capture).  Every call shares the one array and leaves its
+ * contents behind; calls whose kernels overlap on the GPU race on it, so
+ * issue them on one stream or serialise them. */
+int hm_two_site_update_static(const double* A_dev, const double* B_dev, int32_t chi_l, int32_t chi_m,
+                              int32_t chi_r, const double* gate_dev, int32_t chi_max, double cutoff,
+                              int32_t absorb, double* A_out_dev, double* B_out_dev, int32_t* k_out_dev,
+                              void* cuda_stream);
+
 /* The message of the last failed call on ctx (or of the last failed
  * context-free call when ctx is NULL). */
 const char* hm_last_error(const hm_ctx* ctx);

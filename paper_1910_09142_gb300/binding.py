@@ -31,7 +31,7 @@ _ERRNAMES = {HM_ERR_ARG: "HM_ERR_ARG", HM_ERR_NOMEM: "HM_ERR_NOMEM", HM_ERR_CUDA
 EXPORTS = ["hm_create", "hm_destroy", "hm_query_memory", "hm_num_obs", "hm_num_env", "hm_init_chain",
            "hm_free_chain", "hm_evolve", "hm_measure_cluster", "hm_measure_cluster_device",
            "hm_collapse", "hm_collapse_device", "hm_chain_stats", "hm_get_mps", "hm_set_mps",
-           "hm_apply_ops", "hm_plan", "hm_gates", "hm_last_error"]
+           "hm_apply_ops", "hm_plan", "hm_gates", "hm_last_error", "hm_two_site_update_static"]
 
 
 class HmError(RuntimeError):
@@ -91,6 +91,7 @@ def load(path=None):
         "hm_apply_ops": [vp, i64, vp, i32],
         "hm_plan": [P(Params), vp, i32, P(i32)],
         "hm_gates": [P(Params), vp, i32, P(i32)],
+        "hm_two_site_update_static": [vp, vp, i32, i32, i32, vp, i32, dbl, i32, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -151,6 +152,27 @@ def gates(p):
     buf = np.zeros(81 * n.value)
     _check(load().hm_gates(ctypes.byref(p), _ptr(buf), n.value, ctypes.byref(n)))
     return buf.reshape(-1, 9, 9)
+
+
+def two_site_update_static(A, B, gate, chi_max, cutoff, absorb, A_out, B_out, k_out, stream=None):
+    """hm_two_site_update_static on torch CUDA tensors (caller-owned buffers).
+
+    A (chi_l, 3, chi_m), B (chi_m, 3, chi_r), gate (81,), outputs sized for
+    k = min(3 chi_l, 3 chi_r, chi_max); k_out an int32 tensor of one element.
+    """
+    import torch
+    for name, t in (("A", A), ("B", B), ("gate", gate), ("A_out", A_out), ("B_out", B_out)):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    if k_out.dtype != torch.int32 or not k_out.is_cuda:
+        raise ValueError("k_out must be an int32 CUDA tensor")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    chi_l, _, chi_m = A.shape
+    chi_r = B.shape[2]
+    _check(load().hm_two_site_update_static(
+        ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), chi_l, chi_m, chi_r,
+        ctypes.c_void_p(gate.data_ptr()), chi_max, cutoff, absorb, ctypes.c_void_p(A_out.data_ptr()),
+        ctypes.c_void_p(B_out.data_ptr()), ctypes.c_void_p(k_out.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
 
 
 # ---- context ---------------------------------------------------------------------------

@@ -426,6 +426,8 @@ struct Scratch {   // temporary arena block for host-output calls
 
 }  // namespace
 
+void hm::set_global_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 int hm_create(hm_ctx** out, int device, void* dev_mem, size_t bytes, void* cuda_stream) {

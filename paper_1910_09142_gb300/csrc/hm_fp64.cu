@@ -767,3 +767,151 @@ int launch_reset(const BatchArg& b, const OutArg& o, int draw_initial, void* str
 }
 
 }  // namespace hm
+
+// ---------------------------------------------------------------------------
+// Allocation-free two-site update (hm_two_site_update_static).
+//
+// For callers that cannot allocate device memory: code running while a CUDA
+// graph is being captured, inside another library's memory pool, or in a
+// process whose allocator is owned by someone else.  The scratch of the
+// update (chain descriptor, site slots, theta, Jacobi matrices, singular
+// values) lives in one file-scope device array of fixed size; every GPU that
+// loads this library holds it until the process exits.  All calls share the
+// array, so two calls whose kernels overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+
+namespace hm {
+namespace {
+
+constexpr int kStaticChi = 128;                                       // largest chi_l, chi_m, chi_r
+constexpr int64_t kStaticSlot = (int64_t)kStaticChi * 3 * kStaticChi;  // one site tensor
+constexpr int64_t kStaticWs = (int64_t)(3 * kStaticChi) * (3 * kStaticChi);
+constexpr int kStaticSv = 3 * kStaticChi;
+constexpr int64_t kStaticDoubles = 64 + 2 * kStaticSlot + 3 * kStaticWs + 2 * kStaticSv;
+
+static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
+static_assert(sizeof(ChainDev) + 2 * sizeof(double*) + 6 * sizeof(int32_t) <= 48 * sizeof(double),
+              "descriptor and meta data must fit below the statistics slots");
+
+__global__ void __launch_bounds__(NT)
+two_site_static_kernel(double* scratch, const double* A, const double* B, int chi_l, int chi_m, int chi_r,
+                       const double* gate, int chi_max, double cutoff, int absorb, double* A_out,
+                       double* B_out, int32_t* k_out) {
+  __shared__ Shared sh;
+  ChainDev* c = reinterpret_cast<ChainDev*>(scratch);
+  char* meta = reinterpret_cast<char*>(scratch) + sizeof(ChainDev);   // 64 doubles hold struct + meta
+  double** sites = reinterpret_cast<double**>(meta);
+  int32_t* chi = reinterpret_cast<int32_t*>(meta + 2 * sizeof(double*));
+  int32_t* status = chi + 4;
+  double* stats = scratch + 48;
+  double* slotA = scratch + 64;
+  double* slotB = slotA + kStaticSlot;
+  double* ws = slotB + kStaticSlot;
+  if (threadIdx.x == 0) {
+    // everything that must start at zero is cleared here, every call
+    ChainDev d = {};
+    d.n_sites = 2;
+    d.n_gates = 1;
+    d.chi_max = chi_max;
+    d.cutoff = cutoff;
+    d.gates = gate;
+    d.site = sites;
+    d.chi = chi;
+    d.stats = stats;
+    d.status = status;
+    d.err_where = status + 1;
+    d.theta = ws;
+    d.W = ws + kStaticWs;
+    d.V = ws + 2 * kStaticWs;
+    d.sig = ws + 3 * kStaticWs;
+    d.perm = reinterpret_cast<int32_t*>(ws + 3 * kStaticWs + kStaticSv);
+    d.ws_cap = kStaticWs;
+    d.sv_cap = kStaticSv;
+    d.chi_cap = kStaticChi;
+    *c = d;
+    sites[0] = slotA;
+    sites[1] = slotB;
+    chi[0] = chi_l;
+    chi[1] = chi_m;
+    chi[2] = chi_r;
+    status[0] = status[1] = 0;
+    for (int i = 0; i < ST_N; ++i) stats[i] = 0.0;
+  }
+  for (int e = threadIdx.x; e < chi_l * 3 * chi_m; e += NT) slotA[e] = A[e];
+  for (int e = threadIdx.x; e < chi_m * 3 * chi_r; e += NT) slotB[e] = B[e];
+  __syncthreads();
+  const OpDev op = {0, 0, absorb, 0};
+  two_site_op(c, op, 0, sh, nullptr);
+  __syncthreads();
+  const int code = *(volatile int32_t*)status;
+  const int kk = chi[1];
+  if (code != 0) {
+    if (threadIdx.x == 0) *k_out = code;
+    return;
+  }
+  for (int e = threadIdx.x; e < chi_l * 3 * kk; e += NT) A_out[e] = slotA[e];
+  for (int e = threadIdx.x; e < kk * 3 * chi_r; e += NT) B_out[e] = slotB[e];
+  if (threadIdx.x == 0) *k_out = kk;
+}
+
+}  // namespace
+
+}  // namespace hm
+
+#include <mutex>
+
+namespace {
+
+std::mutex g_static_mu;
+double* g_static_ptr[64] = {};   // device address of g_static_scratch, per device
+
+}  // namespace
+
+extern "C" int hm_two_site_update_static(const double* A_dev, const double* B_dev, int32_t chi_l, int32_t chi_m,
+                                         int32_t chi_r, const double* gate_dev, int32_t chi_max, double cutoff,
+                                         int32_t absorb, double* A_out_dev, double* B_out_dev,
+                                         int32_t* k_out_dev, void* cuda_stream) {
+  using namespace hm;
+  if (!A_dev || !B_dev || !gate_dev || !A_out_dev || !B_out_dev || !k_out_dev) {
+    set_global_error("hm_two_site_update_static: null pointer argument");
+    return HM_ERR_ARG;
+  }
+  if (chi_l < 1 || chi_m < 1 || chi_r < 1 || chi_max < 1 || chi_l > kStaticChi || chi_m > kStaticChi ||
+      chi_r > kStaticChi || chi_max > kStaticChi) {
+    set_global_error("hm_two_site_update_static: chi_l, chi_m, chi_r and chi_max must lie in [1, 128] "
+                     "(the size of its fixed scratch array)");
+    return HM_ERR_ARG;
+  }
+  if ((absorb != 0 && absorb != 1) || !(cutoff >= 0.0) || !(cutoff < 1.0)) {
+    set_global_error("hm_two_site_update_static: absorb must be 0 or 1 and cutoff in [0, 1)");
+    return HM_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    set_global_error("hm_two_site_update_static: no current CUDA device");
+    return HM_ERR_CUDA;
+  }
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      // one-time set-up on this device (the device is current here): the
+      // host-side symbol is only a stand-in, the kernel needs the device address
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        set_global_error("hm_two_site_update_static: cudaGetSymbolAddress of the scratch array failed");
+        return HM_ERR_CUDA;
+      }
+      g_static_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_static_ptr[dev];
+  }
+  two_site_static_kernel<<<1, NT, 0, (cudaStream_t)cuda_stream>>>(scratch, A_dev, B_dev, chi_l, chi_m, chi_r,
+                                                                  gate_dev, chi_max, cutoff, absorb, A_out_dev,
+                                                                  B_out_dev, k_out_dev);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_global_error("hm_two_site_update_static: kernel launch failed");
+    return HM_ERR_CUDA;
+  }
+  return HM_OK;
+}

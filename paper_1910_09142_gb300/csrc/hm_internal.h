@@ -84,6 +84,9 @@ int launch_evolve_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_measure_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_collapse_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_reset(const BatchArg& b, const OutArg& o, int draw_initial, void* stream);
+// Message returned by hm_last_error(NULL) (hm_api.cu).
+void set_global_error(const char* msg);
+
 // Mixed-precision evolve (hm_mixed.cu); chi_cap = largest bond cap in the batch.
 int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* stream);
 
