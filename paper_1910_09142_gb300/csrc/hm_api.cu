@@ -225,7 +225,7 @@ struct MemPlan {
   std::vector<int64_t> slot_off;     // byte offsets of site slots
   int64_t ws_cap = 0, env_cap = 0;
   int32_t sv_cap = 0, chi_cap = 0;
-  size_t off_desc, off_ops, off_gates, off_kind, off_mi, off_mj, off_mJ, off_xb, off_siteptr, off_chi,
+  size_t off_desc, off_ops, off_gates, off_kind, off_mi, off_mj, off_mJ, off_ms, off_xb, off_siteptr, off_chi,
       off_env, off_cnt, off_stats, off_status, off_theta, off_W, off_V, off_sig, off_perm, off_envws,
       off_slots, total;
 };
@@ -252,7 +252,12 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops) {
   }
   m.ws_cap = std::max<int64_t>(m.ws_cap, 2 * (int64_t)m.sv_cap + 2);
   if (n == 1) m.ws_cap = 64, m.sv_cap = 3;
-  m.env_cap = 7 * (int64_t)m.chi_cap * m.chi_cap;
+  // transfer workspace: 10 chi x chi matrices + one right environment per
+  // distinct measured end site (measure); the collapse uses the first 7
+  std::vector<int> ends;
+  for (const Bond& b : L.meas)
+    if (std::find(ends.begin(), ends.end(), b.j) == ends.end()) ends.push_back(b.j);
+  m.env_cap = (10 + (int64_t)ends.size()) * m.chi_cap * m.chi_cap;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -266,6 +271,7 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops) {
   m.off_mi = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
   m.off_mj = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
   m.off_mJ = take(std::max<size_t>(L.meas.size(), 1) * sizeof(double));
+  m.off_ms = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
   m.off_xb = take(9 * sizeof(double));
   m.off_siteptr = take(n * sizeof(double*));
   m.off_chi = take((n + 1) * sizeof(int32_t));
@@ -577,6 +583,7 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   d.meas_i = (const int32_t*)(base + mp.off_mi);
   d.meas_j = (const int32_t*)(base + mp.off_mj);
   d.meas_J = (const double*)(base + mp.off_mJ);
+  d.meas_slot = (const int32_t*)(base + mp.off_ms);
   d.xbasis = (const double*)(base + mp.off_xb);
   d.site = (double**)(base + mp.off_siteptr);
   d.chi = (int32_t*)(base + mp.off_chi);
@@ -600,10 +607,17 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   const std::vector<double> g = gate_table(L);
   std::memcpy(img.data() + mp.off_gates, g.data(), g.size() * sizeof(double));
   std::memcpy(img.data() + mp.off_kind, L.kind.data(), L.kind.size() * sizeof(int32_t));
+  std::vector<int> ends;
   for (size_t q = 0; q < L.meas.size(); ++q) {
     ((int32_t*)(img.data() + mp.off_mi))[q] = L.meas[q].i;
     ((int32_t*)(img.data() + mp.off_mj))[q] = L.meas[q].j;
     ((double*)(img.data() + mp.off_mJ))[q] = L.meas[q].J;
+    auto it = std::find(ends.begin(), ends.end(), L.meas[q].j);
+    if (it == ends.end()) {
+      ends.push_back(L.meas[q].j);
+      it = ends.end() - 1;
+    }
+    ((int32_t*)(img.data() + mp.off_ms))[q] = (int32_t)(it - ends.begin());
   }
   const double r = 1.0 / std::sqrt(2.0);
   const double xb[9] = {0.5, r, 0.5, r, 0.0, -r, 0.5, -r, 0.5};

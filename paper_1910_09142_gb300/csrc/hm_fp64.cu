@@ -437,9 +437,27 @@ __device__ __constant__ double kSz[9] = {1, 0, 0, 0, 0, 0, 0, 0, -1};
 __device__ __constant__ double kSp[9] = {0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0, 0, 0};
 __device__ __constant__ double kSm[9] = {0, 0, 0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0};
 
+// Right environment through one site: Rout[i, j] = sum_s A^s Rin A^{sT}
+// (Rin cr x cr, Rout cl x cl).  Y: 3cl x cr scratch.
+__device__ void cta_rtransfer(const double* Rin, const double* A, int cl, int cr, double* Rout, double* Y,
+                              Shared& sh) {
+  if (threadIdx.x == 0) sh.scal[4] += 12.0 * cl * cr * cr;
+  cta_gemm<false, false>(3 * cl, cr, cr, 1.0, A, cr, Rin, cr, 0.0, Y, cr, sh.g);
+  cta_gemm<false, true>(cl, cl, 3 * cr, 1.0, Y, 3 * cr, A, 3 * cr, 0.0, Rout, cl, sh.g);
+}
+
+// sum_{k,l} X[k, l] Y[k, l] over n entries, block-wide.
+__device__ double cta_dot(const double* X, const double* Y, int n, Shared& sh) {
+  double acc = 0.0, d1 = 0.0, d2 = 0.0;
+  for (int e = threadIdx.x; e < n; e += NT) acc = fma(X[e], Y[e], acc);
+  block_sum3(acc, d1, d2, sh);
+  return acc;
+}
+
 // Step 3 (Sec. I.C.1): <S_i.S_j> and <Sz_i Sz_j> on every measured bond.
-// Requires the centre on site 0, so every site >= 1 is right-orthonormal and
-// the right environment of any position is the identity.
+// Right environments are built explicitly from the last site (no reliance on
+// the canonical form), so <psi|psi> is the full contraction and every value
+// is divided by it.
 __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) {
   __shared__ Shared sh;
   ChainDev* c = b.c[blockIdx.x];
@@ -452,18 +470,31 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
   const int64_t cc = (int64_t)c->chi_cap * c->chi_cap;
   double* Lp[2] = {c->env_ws, c->env_ws + cc};
   double* Ep[2] = {c->env_ws + 2 * cc, c->env_ws + 3 * cc};
-  double* Z = c->env_ws + 4 * cc;
-  // <psi|psi> = |A_0|^2 when sites >= 1 are right-orthonormal
-  double nrm = 0.0, d1 = 0.0, d2 = 0.0;
-  {
-    const int sz0 = c->chi[0] * 3 * c->chi[1];
-    for (int e = tid; e < sz0; e += NT) nrm += c->site[0][e] * c->site[0][e];
-    block_sum3(nrm, d1, d2, sh);
-  }
+  double* Z = c->env_ws + 4 * cc;          // 3 cc
+  double* Et = c->env_ws + 7 * cc;         // cc
+  double* Rp[2] = {c->env_ws + 8 * cc, c->env_ws + 9 * cc};
+  double* Rend = c->env_ws + 10 * cc;      // one cc slot per distinct measured end site
   if (tid == 0) {
-    Lp[0][0] = 1.0;
+    Rp[0][0] = 1.0;
     sh.scal[4] = 0.0;
   }
+  __syncthreads();
+  // right sweep: R(pos) = environment of sites >= pos; keep R(b + 1) per end b
+  int rc = 0;
+  for (int pos = c->n_sites - 1; pos >= 0; --pos) {
+    for (int q = 0; q < c->n_meas; ++q) {
+      if (c->meas_j[q] == pos) {            // R(pos + 1) is current
+        const int slot = c->meas_slot[q];
+        const int n2 = c->chi[pos + 1] * c->chi[pos + 1];
+        for (int e = tid; e < n2; e += NT) Rend[(size_t)slot * cc + e] = Rp[rc][e];
+      }
+    }
+    __syncthreads();
+    cta_rtransfer(Rp[rc], c->site[pos], c->chi[pos], c->chi[pos + 1], Rp[rc ^ 1], Z, sh);
+    rc ^= 1;
+  }
+  const double nrm = Rp[rc][0];            // <psi|psi>
+  if (tid == 0) Lp[0][0] = 1.0;
   __syncthreads();
   int pos = 0, cur = 0;
   double E_est = 0.0;
@@ -486,8 +517,11 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
       cta_transfer(Lp[cur], c->site[a], c->chi[a], c->chi[a + 1], ops1[o1], Ep[ec], Z, sh);
       for (int kk = a + 1; kk <= blast; ++kk) {
         for (int q = bi; q < bend; ++q) {
-          if (c->meas_j[q] == kk)
-            vals[o1][q - bi] = cta_close(Ep[ec], c->site[kk], c->chi[kk], c->chi[kk + 1], ops2[o1], Z, sh);
+          if (c->meas_j[q] == kk) {
+            cta_transfer(Ep[ec], c->site[kk], c->chi[kk], c->chi[kk + 1], ops2[o1], Et, Z, sh);
+            const int n2 = c->chi[kk + 1] * c->chi[kk + 1];
+            vals[o1][q - bi] = cta_dot(Et, Rend + (size_t)c->meas_slot[q] * cc, n2, sh);
+          }
         }
         if (kk < blast) {
           cta_transfer(Ep[ec], c->site[kk], c->chi[kk], c->chi[kk + 1], nullptr, Ep[ec ^ 1], Z, sh);

@@ -40,6 +40,7 @@ struct ChainDev {
   const int32_t* meas_i;     // n_meas, sorted by (i, j)
   const int32_t* meas_j;
   const double* meas_J;
+  const int32_t* meas_slot;  // n_meas: index of meas_j among the distinct end sites
   const double* xbasis;      // 9: rows are the Sx eigenvectors (m=+1,0,-1 order)
   // mutable state
   double** site;             // n_sites device pointers (fixed slots)

@@ -96,7 +96,7 @@ def test_samples_match_oracle(ctx):
 
 
 def test_small_config_samples(ctx):
-    """Lx=4 ladder, 2W=4, beta=2, tau=0.1, chi=64, cutoff 1e-12 (3 samples)."""
+    """Lx=4 ladder, 2W=4, beta=2, tau=0.1, chi=64, cutoff 1e-12 (2 samples)."""
     b = _b()
     cfg = dict(Lx=4, two_W=4, J_leg=1.0, J_rung=1.0, beta=2.0, tau=0.1, chi_max=64, cutoff=1e-12)
     p = b.params(**cfg, seed=0, chain_id=0)
@@ -105,7 +105,7 @@ def test_small_config_samples(ctx):
         ref = ochain.HybridChain(seed=0, chain_id=0, **cfg)
         n_obs, n_env = b.num_obs(p), b.num_env(p)
         worst = 0.0
-        for _ in range(3):
+        for _ in range(2):
             ctx.evolve([cid])
             obs = ctx.measure([cid], n_obs)[0]
             env, logp = ctx.collapse([cid], n_env)
