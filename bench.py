@@ -43,13 +43,28 @@ def parse():
     ap.add_argument("--chains", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # workload overrides (smaller cases for profiling; not the headline line)
+    ap.add_argument("--Lx", type=int, default=None)
+    ap.add_argument("--two-W", type=int, default=None)
+    ap.add_argument("--beta", type=float, default=None)
+    ap.add_argument("--chi-max", type=int, default=None)
     return ap.parse_args()
 
 
-def workload_config(args, chains):
+def workload(args):
+    """The benchmark ladder, with any command-line overrides applied."""
     cfg = synth.ladder("ladder16")
-    return {"workload": "S=1 Heisenberg ladder Lx=16 x 2, 2W=8 cluster sites, beta=1, tau=0.05, "
-                        "chi_max=256, cutoff=1e-7, %d chains/GPU" % chains,
+    for key, val in (("Lx", args.Lx), ("two_W", args.two_W), ("beta", args.beta), ("chi_max", args.chi_max)):
+        if val is not None:
+            cfg[key] = val
+    return cfg
+
+
+def workload_config(args, chains):
+    cfg = workload(args)
+    return {"workload": "S=1 Heisenberg ladder Lx=%d x 2, 2W=%d cluster sites, beta=%g, tau=%g, "
+                        "chi_max=%d, cutoff=%g, %d chains/GPU" % (cfg["Lx"], cfg["two_W"], cfg["beta"], cfg["tau"],
+                                                                   cfg["chi_max"], cfg["cutoff"], chains),
             "Lx": cfg["Lx"], "two_W": cfg["two_W"], "beta": cfg["beta"], "tau": cfg["tau"],
             "chi_max": cfg["chi_max"], "cutoff": cfg["cutoff"], "J_leg": cfg["J_leg"],
             "J_rung": cfg["J_rung"], "chains_per_gpu": chains, "precision": args.precision,
@@ -144,7 +159,7 @@ def main():
     if not os.path.exists(build.LIB):
         build.build()
     b = binding
-    cfg = synth.ladder("ladder16")
+    cfg = workload(args)
     prec = b.HM_MIXED if args.precision == "mixed" else b.HM_FP64
     n = args.chains
     ps = [b.params(**cfg, precision=prec, seed=0, chain_id=rank * n + i) for i in range(n)]
@@ -207,8 +222,9 @@ def main():
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 2))
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             ctx.evolve(ids)
             ctx.measure(ids, n_obs)            # host output (D2H inside)
             ctx.collapse(ids, n_env)           # host outputs (D2H inside)
@@ -218,7 +234,7 @@ def main():
             t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda:%d" % local)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
-        e2e = {"value": world * n * args.steps / e2e_s, "unit": "samples/s",
+        e2e = {"value": world * n * e2e_steps / e2e_s, "unit": "samples/s", "steps": e2e_steps,
                "h2d_bytes_per_step": 8 * n,                      # chain handles
                "d2h_bytes_per_step": n * (8 * n_obs + n_env + 8)}
 
