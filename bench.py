@@ -72,6 +72,21 @@ def workload_config(args, chains):
             "parallelism": "independent chains per GPU" if args.gpus > 1 else "1 GPU"}
 
 
+def rank_chain_ids(rank, chains_per_rank):
+    """Chain ids (Philox stream ids) owned by one rank: disjoint across ranks."""
+    return [rank * chains_per_rank + i for i in range(chains_per_rank)]
+
+
+def max_over_ranks(value, dist, device=None):
+    """The largest value over all ranks (the job's time); identity at world size 1."""
+    import torch
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_sample_rate(n_samples=1):
     """The FP64 oracle as it stands: n_samples Markov steps of chain 0, 1 core."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -162,7 +177,7 @@ def main():
     cfg = workload(args)
     prec = b.HM_MIXED if args.precision == "mixed" else b.HM_FP64
     n = args.chains
-    ps = [b.params(**cfg, precision=prec, seed=0, chain_id=rank * n + i) for i in range(n)]
+    ps = [b.params(**cfg, precision=prec, seed=0, chain_id=c) for c in rank_chain_ids(rank, n)]
     per = b.query_memory(ps[0])
     stream = torch.cuda.Stream(local)
     ctx = b.Context(per * n + (512 << 20), device=local, stream=stream)
@@ -213,10 +228,7 @@ def main():
     stats1 = np.array([ctx.stats(c) for c in ids])
     d = stats1 - stats0
     flops_alg = float(d[:, 0].sum() + d[:, 1].sum() + d[:, 2].sum())
-    if world > 1:
-        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda:%d" % local)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(t_ms, dist, "cuda:%d" % local)
     value = world * n * args.steps / (t_ms / 1e3)
 
     e2e = None
@@ -230,10 +242,7 @@ def main():
             ctx.collapse(ids, n_env)           # host outputs (D2H inside)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda:%d" % local)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda:%d" % local)
         e2e = {"value": world * n * e2e_steps / e2e_s, "unit": "samples/s", "steps": e2e_steps,
                "h2d_bytes_per_step": 8 * n,                      # chain handles
                "d2h_bytes_per_step": n * (8 * n_obs + n_env + 8)}
