@@ -155,10 +155,16 @@ __device__ int cta_jacobi(double* __restrict__ W, int q, int p, double* __restri
   for (int e = tid; e < p * p; e += NT) V[e] = (e % (p + 1) == 0) ? 1.0 : 0.0;
   const double tol = sqrt((double)q) * 2.220446049250313e-16;
   const int p2 = p + (p & 1);
-  int sweep = 0;
-  for (; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) sh.ival[0] = 0;
+  int done = 0;
+  bool converged = false;
+  double rmax = 0.0;
+  while (done < kMaxSweeps) {
+    if (tid == 0) {
+      sh.ival[0] = 0;
+      sh.scal[5] = 0.0;                 // largest rotation ratio of the sweep
+    }
     __syncthreads();
+    rmax = 0.0;
     for (int r = 0; r < p2 - 1; ++r) {
       for (int pi = warp; pi < p2 / 2; pi += nwarps) {
         int a, b;
@@ -183,6 +189,7 @@ __device__ int cta_jacobi(double* __restrict__ W, int q, int p, double* __restri
         be = warp_sum(be);
         ga = warp_sum(ga);
         if (ga != 0.0 && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          rmax = fmax(rmax, fabs(ga) / (sqrt(al) * sqrt(be)));
           const double zeta = (be - al) / (2.0 * ga);
           double t;
           if (fabs(zeta) > 1e150) t = 0.5 / zeta;
@@ -205,11 +212,21 @@ __device__ int cta_jacobi(double* __restrict__ W, int q, int p, double* __restri
       }
       __syncthreads();
     }
-    const int rotated = sh.ival[0];
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(&sh.scal[5]),
+                             (unsigned long long)__double_as_longlong(rmax));
     __syncthreads();
-    if (!rotated) break;
+    const int rotated = sh.ival[0];
+    const double rm = sh.scal[5];
+    __syncthreads();
+    ++done;
+    // no rotation: converged; all rotations tiny: quadratic convergence puts
+    // the next sweep's off-diagonals (O(rm^2)) far below the tolerance
+    if (!rotated || rm < 1e-9) {
+      converged = true;
+      break;
+    }
   }
-  return sweep < kMaxSweeps ? sweep + 1 : -1;
+  return converged ? done : -1;
 }
 
 // Truncation rule (Sec. II): smallest k >= 1 whose discarded weight

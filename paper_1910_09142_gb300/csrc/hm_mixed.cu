@@ -102,7 +102,7 @@ __device__ void cta_gemm_f32(int M, int N, int K, const double* __restrict__ A, 
 // Rotate the column pair (x, y) of length q (W) and (vx, vy) of length p (V)
 // so that x . y = 0 (Hestenes).  Warp-cooperative; returns 1 if rotated.
 __device__ __forceinline__ int rotate_pair(float* x, float* y, int q, float* vx, float* vy, int p, float tol,
-                                           int lane) {
+                                           int lane, float* rmax) {
   float al = 0.f, be = 0.f, ga = 0.f;
   for (int i = lane; i < q; i += 32) {
     const float a = x[i], b = y[i];
@@ -114,6 +114,7 @@ __device__ __forceinline__ int rotate_pair(float* x, float* y, int q, float* vx,
   be = warp_sumf(be);
   ga = warp_sumf(ga);
   if (!(ga != 0.f && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return 0;
+  *rmax = fmaxf(*rmax, fabsf(ga) / (sqrtf(al) * sqrtf(be)));
   const float zeta = (be - al) / (2.f * ga);
   float t;
   if (fabsf(zeta) > 1e18f) t = 0.5f / zeta;
@@ -156,11 +157,16 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
   float* svJ = svI + (size_t)b * p;
   const float tol = sqrtf((float)q) * FLT_EPSILON;
   const int nb = (p + b - 1) / b;
-  int sweep = 0;
-  for (; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) sc.ival[0] = 0;
+  int done = 0;
+  bool converged = false;
+  while (done < kMaxSweeps) {
+    if (tid == 0) {
+      sc.ival[0] = 0;
+      sc.ival[2] = 0;                   // largest rotation ratio of the sweep (float bits)
+    }
     __syncthreads();
     int rot = 0;
+    float rmax = 0.f;
     // intra-block pairs: round-robin tournament inside each block
     for (int I = 0; I < nb; ++I) {
       const int c0 = I * b, nc = min(b, p - c0);
@@ -173,7 +179,7 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
           if (pi == 0) { a = r; bb = n2 - 1; } else { a = (r + pi) % (n2 - 1); bb = (r - pi + n2 - 1) % (n2 - 1); }
           if (a >= nc || bb >= nc) continue;
           rot |= rotate_pair(swI + (size_t)a * q, swI + (size_t)bb * q, q, svI + (size_t)a * p, svI + (size_t)bb * p,
-                             p, tol, lane);
+                             p, tol, lane, &rmax);
         }
         __syncthreads();
       }
@@ -194,7 +200,7 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
             const int j = (i + t) % b;
             if (j >= nJ) continue;
             rot |= rotate_pair(swI + (size_t)i * q, swJ + (size_t)j * q, q, svI + (size_t)i * p, svJ + (size_t)j * p,
-                               p, tol, lane);
+                               p, tol, lane, &rmax);
           }
           __syncthreads();
         }
@@ -205,12 +211,20 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
       __syncthreads();
     }
     if (rot && lane == 0) sc.ival[0] = 1;
+    if (lane == 0) atomicMax(&sc.ival[2], __float_as_int(rmax));
     __syncthreads();
     const int any = sc.ival[0];
+    const float rm = __int_as_float(sc.ival[2]);
     __syncthreads();
-    if (!any) break;
+    ++done;
+    // no rotation: converged; all rotations tiny: quadratic convergence puts
+    // the next sweep's off-diagonals (O(rm^2)) below the tolerance
+    if (!any || rm < 2e-4f) {
+      converged = true;
+      break;
+    }
   }
-  return sweep < kMaxSweeps ? sweep + 1 : -1;
+  return converged ? done : -1;
 }
 
 __device__ void set_error(const ChainDev* c, int code, int where, int32_t* ctx_err) {
