@@ -211,3 +211,14 @@ def dense_bond_operator(Lx, a, b, kind):
     if kind == "zz":
         return embed(sz, sz)
     return embed(sz, sz) + 0.5 * (embed(sp, sm) + embed(sm, sp))
+
+
+def total_sz_squared(ed, beta):
+    """<(S^z_tot)^2> = sum_q q^2 Z_q / Z from the S^z-sector spectra (no S.S operators)."""
+    e_min = min(ed.eig(q)[0][0] for q in ed.sectors)
+    z = acc = 0.0
+    for q in ed.sectors:
+        w = np.exp(-beta * (ed.eig(q)[0] - e_min)).sum()
+        z += w
+        acc += q * q * w
+    return acc / z

@@ -16,6 +16,8 @@ Output layout of ``measure`` (also the layout of the CUDA library's output):
   [0]               E_est = sum_b J_b <S_i . S_j>_b over measured bonds
   [1 + 2 b]         <S_i . S_j> of measured bond b (bonds in sorted order)
   [2 + 2 b]         <Sz_i Sz_j> of measured bond b
+``susceptibility`` follows Eq. sus (Sec. II.A): chi = (beta/3) sum_i <S_c . S_i>,
+averaged over the centre sites c of the measured region.
 Pins: ``tests/test_oracle_measure.py`` (dense expectation values, SU(2)
 relation in the pure-ancilla limit, beta = 0 values).
 """
@@ -79,3 +81,25 @@ def measure(mps, bonds):
         out[2 + 2 * b] = zz
         out[0] += J * ss
     return out
+
+
+def susceptibility(mps, ladder, region_sites, beta):
+    """Estimator of the uniform susceptibility of Eq. sus for one sample.
+
+    chi_M = (beta / 3) (1 / |M|) sum_{j in M} sum_{i physical} <S_j . S_i>, with
+    M = ``region_sites`` (MPS indices of physical sites; the paper averages j
+    over the central 6 x 2 block) and i running over every physical site of the
+    ladder, environment included (<S_j . S_j> = s(s+1) = 2).  Returns
+    (chi_M, raw sum).  Written directly from Eq. sus with two-point functions.
+    """
+    envs = environments(mps)
+    phys = [k for k, (kind, _, _) in enumerate(ladder.sites) if kind == "P"]
+    total = 0.0
+    for j in region_sites:
+        for i in phys:
+            if i == j:
+                total += 2.0
+            else:
+                a, b = min(i, j), max(i, j)
+                total += bond_values(mps, envs, a, b)[0]
+    return beta / 3.0 * total / len(region_sites), total
