@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--two-W", type=int, default=None)
     ap.add_argument("--beta", type=float, default=None)
     ap.add_argument("--chi-max", type=int, default=None)
+    ap.add_argument("--susceptibility", action="store_true",
+                    help="after the run, time hm_measure_susceptibility on freshly evolved chains")
     return ap.parse_args()
 
 
@@ -271,6 +273,15 @@ def main():
             "clocks": clk}
     if e2e:
         line["e2e"] = e2e
+    if args.susceptibility:
+        ctx.evolve(ids)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sus = ctx.susceptibility(ids)                 # host output, synchronised
+        sus_s = time.perf_counter() - t0
+        line["susceptibility"] = {"ms_per_call": 1e3 * sus_s, "chains": n,
+                                  "chi_mean": float(sus[:, 0].mean()), "kernel": "susceptibility_fp64_kernel"}
+        ctx.collapse(ids, n_env)
     if not args.no_cpu_baseline and world == 1:
         rate, dt = oracle_sample_rate(1)
         line["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": 1, "kind": "oracle",

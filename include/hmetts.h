@@ -141,6 +141,15 @@ int hm_measure_cluster(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out,
 int hm_measure_cluster_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out_dev,
                               int32_t n_obs);
 
+/* Uniform susceptibility estimator of Eq. sus (Sec. II.A) for n evolved
+ * chains: out[2 i] = chi_M = (beta / 3) (1 / |M|) sum_{j in M} sum_i <S_j . S_i>
+ * and out[2 i + 1] = the double sum itself, where M is the set of physical
+ * sites of the measured columns (see meas_col_lo/hi; the paper averages over
+ * the central 6 x 2 sites) and i runs over every physical site, environment
+ * included (<S_j . S_j> = 2).  HOST output (2 n doubles); binary64; no
+ * canonical-form assumption.  Synchronises. */
+int hm_measure_susceptibility(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out);
+
 /* Step 4: collapse the environment of n evolved chains, left to right, in the
  * basis of their sample index, then reset each chain to the new initial state
  * |i_{n+1}>_E |B>_C.  env_out (HOST, n * n_env, nullable): basis indices of

@@ -31,7 +31,8 @@ _ERRNAMES = {HM_ERR_ARG: "HM_ERR_ARG", HM_ERR_NOMEM: "HM_ERR_NOMEM", HM_ERR_CUDA
 EXPORTS = ["hm_create", "hm_destroy", "hm_query_memory", "hm_num_obs", "hm_num_env", "hm_init_chain",
            "hm_free_chain", "hm_evolve", "hm_measure_cluster", "hm_measure_cluster_device",
            "hm_collapse", "hm_collapse_device", "hm_chain_stats", "hm_get_mps", "hm_set_mps",
-           "hm_apply_ops", "hm_plan", "hm_gates", "hm_last_error", "hm_two_site_update_static"]
+           "hm_apply_ops", "hm_plan", "hm_gates", "hm_last_error", "hm_two_site_update_static",
+           "hm_measure_susceptibility"]
 
 
 class HmError(RuntimeError):
@@ -91,6 +92,7 @@ def load(path=None):
         "hm_apply_ops": [vp, i64, vp, i32],
         "hm_plan": [P(Params), vp, i32, P(i32)],
         "hm_gates": [P(Params), vp, i32, P(i32)],
+        "hm_measure_susceptibility": [vp, P(i64), i32, vp],
         "hm_two_site_update_static": [vp, vp, i32, i32, i32, vp, i32, dbl, i32, vp, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -226,6 +228,13 @@ class Context:
         arr, ptr = _ids(ids)
         self._c(self.lib.hm_measure_cluster_device(self.h, ptr, len(arr), ctypes.c_void_p(out_tensor.data_ptr()),
                                                    out_tensor.shape[-1]))
+
+    def susceptibility(self, ids):
+        """(chi_M, double sum) per chain, Eq. sus."""
+        arr, ptr = _ids(ids)
+        out = np.zeros((len(arr), 2))
+        self._c(self.lib.hm_measure_susceptibility(self.h, ptr, len(arr), _ptr(out)))
+        return out
 
     def collapse(self, ids, n_env):
         arr, ptr = _ids(ids)

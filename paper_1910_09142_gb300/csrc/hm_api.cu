@@ -46,6 +46,7 @@ struct Layout {
   std::vector<int> cluster_cols;
   std::vector<Bond> bonds;            // sorted by (i, j)
   std::vector<Bond> meas;             // measured bonds, sorted
+  std::vector<int32_t> region;        // physical sites of the measured columns, sorted
   int n_steps = 0;
   double tau_eff = 0.0;
 };
@@ -114,6 +115,8 @@ Layout make_layout(const hm_params& p) {
     for (int y = 0; y < 2; ++y) inside[L.phys[2 * x + y]] = 1;
   for (const Bond& b : L.bonds)
     if (inside[b.i] && inside[b.j]) L.meas.push_back(b);
+  for (int k = 0; k < L.n_sites; ++k)
+    if (inside[k]) L.region.push_back(k);
   if (p.beta == 0.0) {
     L.n_steps = 0;
     L.tau_eff = p.tau;
@@ -225,7 +228,7 @@ struct MemPlan {
   std::vector<int64_t> slot_off;     // byte offsets of site slots
   int64_t ws_cap = 0, env_cap = 0;
   int32_t sv_cap = 0, chi_cap = 0;
-  size_t off_desc, off_ops, off_gates, off_kind, off_mi, off_mj, off_mJ, off_ms, off_xb, off_siteptr, off_chi,
+  size_t off_desc, off_ops, off_gates, off_kind, off_mi, off_mj, off_mJ, off_ms, off_reg, off_xb, off_siteptr, off_chi,
       off_env, off_cnt, off_stats, off_status, off_theta, off_W, off_V, off_sig, off_perm, off_envws,
       off_slots, total;
 };
@@ -257,7 +260,9 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops) {
   std::vector<int> ends;
   for (const Bond& b : L.meas)
     if (std::find(ends.begin(), ends.end(), b.j) == ends.end()) ends.push_back(b.j);
-  m.env_cap = (10 + (int64_t)ends.size()) * m.chi_cap * m.chi_cap;
+  // the susceptibility sweeps use 20 matrices + 4 stored per region site
+  m.env_cap = std::max<int64_t>(10 + (int64_t)ends.size(), 20 + 4 * (int64_t)L.region.size()) * m.chi_cap *
+              m.chi_cap;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -272,6 +277,7 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops) {
   m.off_mj = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
   m.off_mJ = take(std::max<size_t>(L.meas.size(), 1) * sizeof(double));
   m.off_ms = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
+  m.off_reg = take(std::max<size_t>(L.region.size(), 1) * sizeof(int32_t));
   m.off_xb = take(9 * sizeof(double));
   m.off_siteptr = take(n * sizeof(double*));
   m.off_chi = take((n + 1) * sizeof(int32_t));
@@ -584,6 +590,8 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   d.meas_j = (const int32_t*)(base + mp.off_mj);
   d.meas_J = (const double*)(base + mp.off_mJ);
   d.meas_slot = (const int32_t*)(base + mp.off_ms);
+  d.region = (const int32_t*)(base + mp.off_reg);
+  d.n_region = (int32_t)L.region.size();
   d.xbasis = (const double*)(base + mp.off_xb);
   d.site = (double**)(base + mp.off_siteptr);
   d.chi = (int32_t*)(base + mp.off_chi);
@@ -619,6 +627,8 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
     }
     ((int32_t*)(img.data() + mp.off_ms))[q] = (int32_t)(it - ends.begin());
   }
+  if (!L.region.empty())
+    std::memcpy(img.data() + mp.off_reg, L.region.data(), L.region.size() * sizeof(int32_t));
   const double r = 1.0 / std::sqrt(2.0);
   const double xb[9] = {0.5, r, 0.5, r, 0.0, -r, 0.5, -r, 0.5};
   std::memcpy(img.data() + mp.off_xb, xb, sizeof xb);
@@ -736,6 +746,39 @@ int hm_measure_cluster(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out,
   if (rc) return rc;
   HM_CUDA(ctx, cudaMemcpyAsync(out, sc.ptr, (size_t)n * n_obs * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_device_error(ctx);
+}
+
+int hm_measure_susceptibility(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out) {
+  if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
+  if (n == 0) return HM_OK;
+  if (!out) return fail(&ctx->err, HM_ERR_ARG, "null output");
+  std::vector<Chain*> cs;
+  int rc = lookup(ctx, ids, n, &cs);
+  if (rc) return rc;
+  for (Chain* c : cs)
+    if (c->phase != 1) return fail(&ctx->err, HM_ERR_STATE, "the susceptibility needs an evolved chain");
+  HM_CUDA(ctx, cudaSetDevice(ctx->device));
+  Scratch sc{ctx};
+  rc = sc.get((size_t)n * sizeof(double));
+  if (rc) return rc;
+  OutArg o{};
+  o.ctx_err = ctx->err_word;
+  o.n_obs = 1;
+  rc = for_batches(cs, [&](BatchArg& b, int s) {
+    o.obs = (double*)sc.ptr + s;
+    return launch_susceptibility_fp64(b, o, ctx->stream);
+  });
+  if (rc != HM_OK) return fail(&ctx->err, rc, "susceptibility launch failed");
+  std::vector<double> raw(n);
+  HM_CUDA(ctx, cudaMemcpyAsync(raw.data(), sc.ptr, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  rc = check_device_error(ctx);
+  if (rc) return rc;
+  for (int32_t i = 0; i < n; ++i) {
+    const double nr = (double)cs[i]->L.region.size();
+    out[2 * i] = cs[i]->p.beta / 3.0 * raw[i] / nr;
+    out[2 * i + 1] = raw[i];
+  }
+  return HM_OK;
 }
 
 static int collapse_impl(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_dev, double* logp_dev,

@@ -563,6 +563,164 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
   }
 }
 
+// Right environment with an operator on this site, accumulated:
+// Rout <- acc * Rout + sum_{s,t} O[s][t] A^s Rin A^{tT}  (O == nullptr: identity;
+// bra index s first).  Rin cr x cr, Rout cl x cl, Y: 3cl x cr scratch.
+__device__ void cta_rtransfer_op(const double* Rin, const double* A, int cl, int cr, const double* O, double* Rout,
+                                 double* Y, double acc, Shared& sh) {
+  if (threadIdx.x == 0) sh.scal[4] += 12.0 * cl * cr * cr;
+  cta_gemm<false, false>(3 * cl, cr, cr, 1.0, A, cr, Rin, cr, 0.0, Y, cr, sh.g);
+  if (O) {
+    for (int e = threadIdx.x; e < cl * cr; e += NT) {
+      const int i = e / cr, r = e % cr;
+      double* y = Y + (size_t)i * 3 * cr + r;
+      const double y0 = y[0], y1 = y[cr], y2 = y[2 * cr];
+      y[0] = O[0] * y0 + O[3] * y1 + O[6] * y2;
+      y[cr] = O[1] * y0 + O[4] * y1 + O[7] * y2;
+      y[2 * cr] = O[2] * y0 + O[5] * y1 + O[8] * y2;
+    }
+    __syncthreads();
+  }
+  cta_gemm<false, true>(cl, cl, 3 * cr, 1.0, Y, 3 * cr, A, 3 * cr, acc, Rout, cl, sh.g);
+}
+
+// Left environment with an operator on this site, accumulated:
+// Eout <- acc * Eout + sum_{s,t} O[s][t] A^{sT} Ein A^t.
+__device__ void cta_transfer_acc(const double* Ein, const double* A, int cl, int cr, const double* O, double* Eout,
+                                 double* Z, double acc, Shared& sh) {
+  if (threadIdx.x == 0) sh.scal[4] += 6.0 * cl * cl * cr + 6.0 * cl * cr * cr;
+  cta_gemm<false, false>(cl, 3 * cr, cl, 1.0, Ein, cl, A, 3 * cr, 0.0, Z, 3 * cr, sh.g);
+  if (O) {
+    for (int e = threadIdx.x; e < cl * cr; e += NT) {
+      const int i = e / cr, r = e % cr;
+      double* z = Z + (size_t)i * 3 * cr + r;
+      const double z0 = z[0], z1 = z[cr], z2 = z[2 * cr];
+      z[0] = O[0] * z0 + O[1] * z1 + O[2] * z2;
+      z[cr] = O[3] * z0 + O[4] * z1 + O[5] * z2;
+      z[2 * cr] = O[6] * z0 + O[7] * z1 + O[8] * z2;
+    }
+    __syncthreads();
+  }
+  cta_gemm<true, false>(cr, cr, 3 * cl, 1.0, A, cr, Z, cr, acc, Eout, cr, sh.g);
+}
+
+// Uniform susceptibility (Eq. sus, Sec. II.A): the double sum
+// sum_{a in M} sum_{b physical} <S_a . S_b> / <psi|psi>, written to o.obs[chain].
+// A right sweep carries the plain right environment R and the running sums
+// R_z, R_-, R_+ of right environments with S^z, S^-, S^+ inserted on every
+// physical site to the right, and keeps all four at each region site a
+// (R(a+1)); a left sweep carries the mirrored sums L, L_z, L_+, L_- and
+// closes, at each region site a, O_a on L against the right sums (b > a)
+// and the left sums with O_a against R (b < a).  Linear in the chain length.
+__global__ void __launch_bounds__(NT) susceptibility_fp64_kernel(BatchArg b, OutArg o) {
+  __shared__ Shared sh;
+  ChainDev* c = b.c[blockIdx.x];
+  const int tid = threadIdx.x;
+  double* out = o.obs + blockIdx.x;
+  if (*(volatile int32_t*)c->status != 0) {
+    if (tid == 0) *out = NAN;
+    return;
+  }
+  const int64_t cc = (int64_t)c->chi_cap * c->chi_cap;
+  double* Rc[4];
+  double* Rn[4];
+  double* Lc[4];
+  double* Ln[4];
+  for (int qq = 0; qq < 4; ++qq) {
+    Rc[qq] = c->env_ws + qq * cc;
+    Rn[qq] = c->env_ws + (4 + qq) * cc;
+    Lc[qq] = c->env_ws + (8 + qq) * cc;
+    Ln[qq] = c->env_ws + (12 + qq) * cc;
+  }
+  double* Z = c->env_ws + 16 * cc;         // 3 cc
+  double* Et = c->env_ws + 19 * cc;
+  double* store = c->env_ws + 20 * cc;     // 4 cc per region site
+  // right sums carry S^z, S^-, S^+ ; left sums carry S^z, S^+, S^-
+  const double* ropk[4] = {nullptr, kSz, kSm, kSp};
+  const double* lopk[4] = {nullptr, kSz, kSp, kSm};
+  if (tid == 0) {
+    Rc[0][0] = 1.0;
+    Rc[1][0] = Rc[2][0] = Rc[3][0] = 0.0;
+    Lc[0][0] = 1.0;
+    Lc[1][0] = Lc[2][0] = Lc[3][0] = 0.0;
+    sh.scal[4] = 0.0;
+  }
+  __syncthreads();
+  const int n = c->n_sites;
+  int amax = -1;
+  for (int s2 = 0; s2 < c->n_region; ++s2) amax = max(amax, c->region[s2]);
+  for (int pos = n - 1; pos >= 0; --pos) {
+    const int cl = c->chi[pos], cr = c->chi[pos + 1];
+    int slot = -1;
+    for (int s2 = 0; s2 < c->n_region; ++s2)
+      if (c->region[s2] == pos) slot = s2;
+    if (slot >= 0) {
+      for (int qq = 0; qq < 4; ++qq)
+        for (int e = tid; e < cr * cr; e += NT) store[(size_t)(4 * slot + qq) * cc + e] = Rc[qq][e];
+      __syncthreads();
+    }
+    const double* A = c->site[pos];
+    const bool phys = c->site_kind[pos] != SITE_ANC;
+    cta_rtransfer_op(Rc[0], A, cl, cr, nullptr, Rn[0], Z, 0.0, sh);
+    for (int qq = 1; qq < 4; ++qq) {
+      cta_rtransfer_op(Rc[qq], A, cl, cr, nullptr, Rn[qq], Z, 0.0, sh);
+      if (phys) cta_rtransfer_op(Rc[0], A, cl, cr, ropk[qq], Rn[qq], Z, 1.0, sh);
+    }
+    for (int qq = 0; qq < 4; ++qq) {
+      double* t = Rc[qq];
+      Rc[qq] = Rn[qq];
+      Rn[qq] = t;
+    }
+  }
+  const double nrm = Rc[0][0];             // <psi|psi>
+  double total = 0.0;
+  for (int pos = 0; pos <= amax; ++pos) {
+    const int cl = c->chi[pos], cr = c->chi[pos + 1];
+    const double* A = c->site[pos];
+    int slot = -1;
+    for (int s2 = 0; s2 < c->n_region; ++s2)
+      if (c->region[s2] == pos) slot = s2;
+    if (slot >= 0) {
+      const double* R0 = store + (size_t)(4 * slot) * cc;
+      const double* Rz = R0 + cc;
+      const double* Rm = R0 + 2 * cc;
+      const double* Rp = R0 + 3 * cc;
+      const int n2 = cr * cr;
+      // b > a: O_a on L, closed against the right sums
+      cta_transfer_acc(Lc[0], A, cl, cr, kSz, Et, Z, 0.0, sh);
+      total += cta_dot(Et, Rz, n2, sh);
+      cta_transfer_acc(Lc[0], A, cl, cr, kSp, Et, Z, 0.0, sh);
+      total += 0.5 * cta_dot(Et, Rm, n2, sh);
+      cta_transfer_acc(Lc[0], A, cl, cr, kSm, Et, Z, 0.0, sh);
+      total += 0.5 * cta_dot(Et, Rp, n2, sh);
+      // b < a: left sums with O_a, closed against R
+      cta_transfer_acc(Lc[1], A, cl, cr, kSz, Et, Z, 0.0, sh);
+      total += cta_dot(Et, R0, n2, sh);
+      cta_transfer_acc(Lc[2], A, cl, cr, kSm, Et, Z, 0.0, sh);
+      total += 0.5 * cta_dot(Et, R0, n2, sh);
+      cta_transfer_acc(Lc[3], A, cl, cr, kSp, Et, Z, 0.0, sh);
+      total += 0.5 * cta_dot(Et, R0, n2, sh);
+      total += 2.0 * nrm;                  // b = a: S.S = s(s+1) = 2
+    }
+    if (pos == amax) break;
+    const bool phys = c->site_kind[pos] != SITE_ANC;
+    cta_transfer_acc(Lc[0], A, cl, cr, nullptr, Ln[0], Z, 0.0, sh);
+    for (int qq = 1; qq < 4; ++qq) {
+      cta_transfer_acc(Lc[qq], A, cl, cr, nullptr, Ln[qq], Z, 0.0, sh);
+      if (phys) cta_transfer_acc(Lc[0], A, cl, cr, lopk[qq], Ln[qq], Z, 1.0, sh);
+    }
+    for (int qq = 0; qq < 4; ++qq) {
+      double* t = Lc[qq];
+      Lc[qq] = Ln[qq];
+      Ln[qq] = t;
+    }
+  }
+  if (tid == 0) {
+    *out = total / nrm;
+    c->stats[ST_TRANSFER] += sh.scal[4];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step 4: collapse and reset.
 // ---------------------------------------------------------------------------
@@ -799,6 +957,12 @@ int launch_evolve_fp64(const BatchArg& b, const OutArg& o, void* stream) {
 int launch_measure_fp64(const BatchArg& b, const OutArg& o, void* stream) {
   if (b.n <= 0) return HM_OK;
   measure_fp64_kernel<<<b.n, NT, 0, (cudaStream_t)stream>>>(b, o);
+  return check_launch();
+}
+
+int launch_susceptibility_fp64(const BatchArg& b, const OutArg& o, void* stream) {
+  if (b.n <= 0) return HM_OK;
+  susceptibility_fp64_kernel<<<b.n, NT, 0, (cudaStream_t)stream>>>(b, o);
   return check_launch();
 }
 

@@ -41,6 +41,8 @@ struct ChainDev {
   const int32_t* meas_j;
   const double* meas_J;
   const int32_t* meas_slot;  // n_meas: index of meas_j among the distinct end sites
+  const int32_t* region;     // n_region physical sites of the measured columns (sorted)
+  int32_t n_region, pad1;
   const double* xbasis;      // 9: rows are the Sx eigenvectors (m=+1,0,-1 order)
   // mutable state
   double** site;             // n_sites device pointers (fixed slots)
@@ -85,6 +87,8 @@ int launch_evolve_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_measure_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_collapse_fp64(const BatchArg& b, const OutArg& o, void* stream);
 int launch_reset(const BatchArg& b, const OutArg& o, int draw_initial, void* stream);
+// Susceptibility double sum (Eq. sus), raw and unnormalised by beta: o.obs[i].
+int launch_susceptibility_fp64(const BatchArg& b, const OutArg& o, void* stream);
 // Message returned by hm_last_error(NULL) (hm_api.cu).
 void set_global_error(const char* msg);
 
