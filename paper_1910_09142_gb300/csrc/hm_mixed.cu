@@ -144,6 +144,122 @@ __device__ void unstage(float* W, float* V, int q, int p, int c0, int nc, const 
   for (int e = threadIdx.x; e < nc * p; e += NT) V[(size_t)c0 * p + e] = sv[e];
 }
 
+// Cross pairs of the block Jacobi with the I column in registers: in every
+// round t warp w pairs column I_w with J_{(w+t) mod b}, so warp w keeps I_w
+// (and its V column) in registers for all later blocks J and only the J
+// column crosses shared memory (one load and one store per element of W and
+// of V).  Column norms are cached in `norm` (recomputed here first), so each
+// rotation needs one dot product.  q <= 32 QL.
+template <int QL>
+__device__ void cross_phase_reg(float* W, float* V, int q, int p, int b, int nb, float* swJ, float* svJ,
+                                float* norm, float tol, int& rot, float& rmax) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarps = NT / 32;
+  for (int j = warp; j < p; j += nwarps) {
+    const float* cj = W + (size_t)j * q;
+    float s2 = 0.f;
+    for (int i = lane; i < q; i += 32) s2 = fmaf(cj[i], cj[i], s2);
+    s2 = warp_sumf(s2);
+    if (lane == 0) norm[j] = s2;
+  }
+  __syncthreads();
+  for (int I = 0; I + 1 < nb; ++I) {
+    const int cI = I * b, nI = min(b, p - cI);
+    const bool own = warp < nI;
+    const int col = cI + warp;
+    float xr[QL], vr[QL];
+    float nx = 0.f;
+#pragma unroll
+    for (int k = 0; k < QL; ++k) {
+      xr[k] = 0.f;
+      vr[k] = 0.f;
+    }
+    if (own) {
+      const float* xw = W + (size_t)col * q;
+      const float* vw = V + (size_t)col * p;
+#pragma unroll
+      for (int k = 0; k < QL; ++k) {
+        if (32 * k >= q) break;               // warp-uniform: only live chunks
+        const int i = lane + 32 * k;
+        xr[k] = i < q ? xw[i] : 0.f;
+        vr[k] = i < p ? vw[i] : 0.f;
+      }
+      nx = norm[col];
+    }
+    for (int J = I + 1; J < nb; ++J) {
+      const int cJ = J * b, nJ = min(b, p - cJ);
+      for (int e = tid; e < nJ * q; e += NT) swJ[e] = W[(size_t)cJ * q + e];
+      for (int e = tid; e < nJ * p; e += NT) svJ[e] = V[(size_t)cJ * p + e];
+      __syncthreads();
+      for (int t = 0; t < b; ++t) {
+        const int j = (warp + t) % b;
+        if (own && j < nJ) {
+          float* y = swJ + (size_t)j * q;
+          float* vy = svJ + (size_t)j * p;
+          float yr[QL];
+          float ga = 0.f;
+#pragma unroll
+          for (int k = 0; k < QL; ++k) {
+            if (32 * k >= q) break;
+            const int i = lane + 32 * k;
+            yr[k] = i < q ? y[i] : 0.f;
+            ga = fmaf(xr[k], yr[k], ga);
+          }
+          ga = warp_sumf(ga);
+          const float be = norm[cJ + j];
+          if (ga != 0.f && nx > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(nx) * sqrtf(be)) {
+            rmax = fmaxf(rmax, fabsf(ga) / (sqrtf(nx) * sqrtf(be)));
+            const float zeta = (be - nx) / (2.f * ga);
+            float tt;
+            if (fabsf(zeta) > 1e18f) tt = 0.5f / zeta;
+            else tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            const float cs = rsqrtf(1.f + tt * tt), sn = cs * tt;
+#pragma unroll
+            for (int k = 0; k < QL; ++k) {
+              if (32 * k >= q) break;
+              const int i = lane + 32 * k;
+              const float a = xr[k], bb = yr[k];
+              xr[k] = cs * a - sn * bb;
+              if (i < q) y[i] = sn * a + cs * bb;
+            }
+#pragma unroll
+            for (int k = 0; k < QL; ++k) {
+              if (32 * k >= p) break;
+              const int i = lane + 32 * k;
+              if (i < p) {
+                const float a = vr[k], bb = vy[i];
+                vr[k] = cs * a - sn * bb;
+                vy[i] = sn * a + cs * bb;
+              }
+            }
+            nx -= tt * ga;
+            __syncwarp();
+            if (lane == 0) norm[cJ + j] = be + tt * ga;
+            rot = 1;
+          }
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < nJ * q; e += NT) W[(size_t)cJ * q + e] = swJ[e];
+      for (int e = tid; e < nJ * p; e += NT) V[(size_t)cJ * p + e] = svJ[e];
+      __syncthreads();
+    }
+    if (own) {
+      float* xw = W + (size_t)col * q;
+      float* vw = V + (size_t)col * p;
+#pragma unroll
+      for (int k = 0; k < QL; ++k) {
+        if (32 * k >= q) break;
+        const int i = lane + 32 * k;
+        if (i < q) xw[i] = xr[k];
+        if (i < p) vw[i] = vr[k];
+      }
+      if (lane == 0) norm[col] = nx;
+    }
+    __syncthreads();
+  }
+}
+
 // Block one-sided Jacobi on W (q x p column-major, q >= p) with V (p x p).
 // smem holds two blocks of b columns of W and of V.  Returns sweeps or -1.
 __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* smem, Scal& sc) {
@@ -188,6 +304,9 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
     }
     // cross pairs of two different blocks: round t pairs column i of I with
     // column (i + t) mod b of J, b disjoint pairs per round
+    if (q > 128 && q <= 32 * 24 && b <= nwarps) {
+      cross_phase_reg<24>(W, V, q, p, b, nb, swJ, svJ, svJ + (size_t)b * p, tol, rot, rmax);
+    } else
     for (int I = 0; I < nb; ++I) {
       const int cI = I * b, nI = min(b, p - cI);
       stage(W, V, q, p, cI, nI, swI, svI);
@@ -411,9 +530,9 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
 size_t mixed_smem_bytes(int chi_cap, int* bcols) {
   const size_t qp = 6 * (size_t)chi_cap;        // q + p <= 3 chi + 3 chi
   int b = 16;
-  while (b > 2 && 2 * (size_t)b * qp * sizeof(float) > 200 * 1024) b /= 2;
+  while (b > 2 && (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float) > 210 * 1024) b /= 2;
   *bcols = b;
-  size_t bytes = 2 * (size_t)b * qp * sizeof(float);
+  size_t bytes = (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float);   // + cached column norms
   const size_t gemm = 2 * GK * GM * sizeof(float);
   return bytes > gemm ? bytes : gemm;
 }
