@@ -262,7 +262,8 @@ __device__ void cross_phase_reg(float* W, float* V, int q, int p, int b, int nb,
 
 // Block one-sided Jacobi on W (q x p column-major, q >= p) with V (p x p).
 // smem holds two blocks of b columns of W and of V.  Returns sweeps or -1.
-__device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* smem, Scal& sc) {
+// tmp: q p + p p floats of scratch (used once, to order the columns).
+__device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* smem, Scal& sc, float* tmp) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = NT / 32;
   for (int e = tid; e < p * p; e += NT) V[e] = (e % (p + 1) == 0) ? 1.f : 0.f;
@@ -275,6 +276,36 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
   const int nb = (p + b - 1) / b;
   int done = 0;
   bool converged = false;
+  {
+    // order the columns by decreasing norm before the first sweep (W and V
+    // permuted together, so W = X V still holds): the graded two-site
+    // matrices converge in ~1 sweep fewer (12.3 -> 11.3 for 256 < p <= 512)
+    float* nrm = svJ + (size_t)b * p;
+    int* rk = reinterpret_cast<int*>(swI);
+    for (int j = warp; j < p; j += nwarps) {
+      const float* cj = W + (size_t)j * q;
+      float s2 = 0.f;
+      for (int i = lane; i < q; i += 32) s2 = fmaf(cj[i], cj[i], s2);
+      s2 = warp_sumf(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
+    __syncthreads();
+    for (int j = tid; j < p; j += NT) {
+      const float nj = nrm[j];
+      int r = 0;
+      for (int i = 0; i < p; ++i) r += (nrm[i] > nj) || (nrm[i] == nj && i < j);
+      rk[j] = r;
+    }
+    __syncthreads();
+    float* tW = tmp;
+    float* tV = tmp + (size_t)q * p;
+    for (int e = tid; e < q * p; e += NT) tW[(size_t)rk[e / q] * q + e % q] = W[e];
+    for (int e = tid; e < p * p; e += NT) tV[(size_t)rk[e / p] * p + e % p] = V[e];
+    __syncthreads();
+    for (int e = tid; e < q * p; e += NT) W[e] = tW[e];
+    for (int e = tid; e < p * p; e += NT) V[e] = tV[e];
+    __syncthreads();
+  }
   while (done < kMaxSweeps) {
     if (tid == 0) {
       sc.ival[0] = 0;
@@ -411,7 +442,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
   }
   __syncthreads();
 
-  const int sweeps = cta_jacobi_f32(W, q, p, V, bcols, smem, sc);
+  const int sweeps = cta_jacobi_f32(W, q, p, V, bcols, smem, sc, theta);   // theta is free here
   if (sweeps < 0) {
     set_error(c, HM_ERR_NUMERIC, t, ctx_err);
     return;
