@@ -1,0 +1,166 @@
+"""Continuous-batching sampling server over the C ABI.
+
+A job asks for ``n_samples`` Markov steps of one hybrid-METTS chain
+(Sec. I.C.1) with its own parameters (ladder length, cluster size, beta,
+chi_max, ...).  The server keeps every admitted chain's MPS resident on the
+device and, on every tick, advances *all* resident chains by one Markov step
+in one batched call per stage (``hm_evolve``, ``hm_measure_cluster``,
+``hm_collapse``), whatever their sizes.  Jobs that arrive while others run
+wait in a FIFO queue and are admitted at the next tick boundary as soon as
+the arena bytes ``hm_query_memory`` reports for them are free and a batch
+slot is open; a finished job's chain is freed at once.  Each chain's result
+depends only on its own data (one CTA per chain), so a job's samples are the
+same alone and in the mix: bit-identical in binary64, and within the stated
+tolerance in the mixed-precision mode, whose column-block size follows the
+largest bond cap in the batch.
+
+All arithmetic of a step runs in ``libhmetts.so``; this module only
+schedules.  Latency of a sample = wall time of the tick that produced it;
+a job's queueing delay is reported separately.
+"""
+import collections
+import time
+
+import numpy as np
+
+from . import binding
+
+
+class Job:
+    """One sampling request; ``results`` gets one observable vector per kept sample."""
+
+    def __init__(self, job_id, params, n_samples, n_warmup=0, arrival=None):
+        self.id = job_id
+        self.params = params                 # binding.Params
+        self.n_samples = int(n_samples)
+        self.n_warmup = int(n_warmup)
+        self.arrival = arrival
+        self.admitted = None
+        self.finished = None
+        self.chain = None
+        self.done_steps = 0
+        self.results = []                    # observable vectors of kept samples
+        self.env = []                        # collapse outcomes of every step
+        self.latencies = []                  # seconds per kept sample
+        self.bytes = 0
+
+    @property
+    def complete(self):
+        return self.done_steps >= self.n_warmup + self.n_samples
+
+
+class Server:
+    """FIFO admission by arena bytes and batch slots; one batched step per tick."""
+
+    def __init__(self, ctx, arena_bytes, max_chains=448, clock=time.perf_counter,
+                 query_memory=None, num_obs=None, num_env=None):
+        self.ctx = ctx
+        self.capacity = int(arena_bytes)
+        self.max_chains = int(max_chains)
+        self.clock = clock
+        self.query_memory = query_memory or binding.query_memory
+        self.num_obs = num_obs or binding.num_obs
+        self.num_env = num_env or binding.num_env
+        self.queue = collections.deque()
+        self.active = []
+        self.finished = []
+        self.used = 0
+        self.ticks = 0
+        self.samples = 0
+        self.busy_s = 0.0
+        self._next_id = 0
+
+    # -- requests ---------------------------------------------------------------------
+    def submit(self, params, n_samples, n_warmup=0):
+        """Queue a job; returns it.  ``params`` is a binding.Params."""
+        job = Job(self._next_id, params, n_samples, n_warmup, self.clock())
+        job.bytes = self.query_memory(params)
+        if job.bytes > self.capacity:
+            raise ValueError("job %d needs %d bytes, more than the whole arena" % (job.id, job.bytes))
+        self._next_id += 1
+        self.queue.append(job)
+        return job
+
+    def _admit(self):
+        while self.queue and len(self.active) < self.max_chains:
+            job = self.queue[0]
+            if self.used + job.bytes > self.capacity:
+                break                                  # FIFO: later jobs wait behind it
+            self.queue.popleft()
+            job.chain = self.ctx.init_chain(job.params)
+            job.admitted = self.clock()
+            self.used += job.bytes
+            self.active.append(job)
+
+    # -- one tick -----------------------------------------------------------------------
+    def step(self):
+        """Admit what fits, then one Markov step of every resident chain.
+
+        Returns the number of chains stepped (0 when idle).
+        """
+        self._admit()
+        if not self.active:
+            return 0
+        t0 = self.clock()
+        ids = [j.chain for j in self.active]
+        self.ctx.evolve(ids)
+        obs = {}
+        for n_obs, group in self._groups(self.num_obs).items():
+            vals = self.ctx.measure([j.chain for j in group], n_obs)
+            for j, v in zip(group, vals):
+                obs[j.id] = v
+        for n_env, group in self._groups(self.num_env).items():
+            env, _ = self.ctx.collapse([j.chain for j in group], n_env)
+            for j, e in zip(group, env):
+                j.env.append(np.array(e))
+        t1 = self.clock()
+        dt = t1 - t0
+        self.busy_s += dt
+        self.ticks += 1
+        still = []
+        for j in self.active:
+            if j.done_steps >= j.n_warmup:
+                j.results.append(obs[j.id])
+                j.latencies.append(dt)
+                self.samples += 1
+            j.done_steps += 1
+            if j.complete:
+                self.ctx.free_chain(j.chain)
+                self.used -= j.bytes
+                j.finished = t1
+                self.finished.append(j)
+            else:
+                still.append(j)
+        self.active = still
+        return len(ids)
+
+    def _groups(self, count):
+        groups = collections.OrderedDict()
+        for j in self.active:
+            groups.setdefault(count(j.params), []).append(j)
+        return groups
+
+    def run(self, arrivals=()):
+        """Serve until idle.  ``arrivals``: iterable of (tick, params, n_samples,
+        n_warmup); a job listed for tick t is submitted before the t-th tick of
+        this call runs (immediately when the server would otherwise idle)."""
+        pending = collections.deque(sorted(arrivals, key=lambda a: a[0]))
+        tick = 0
+        while True:
+            while pending and (pending[0][0] <= tick or (not self.active and not self.queue)):
+                _, p, n, w = pending.popleft()
+                self.submit(p, n, w)
+            if self.step() == 0 and not self.queue and not pending:
+                return self.stats()
+            tick += 1
+
+    # -- statistics ---------------------------------------------------------------------
+    def stats(self):
+        lat = [x for j in self.finished + self.active for x in j.latencies]
+        waits = [j.admitted - j.arrival for j in self.finished + self.active if j.admitted is not None]
+        return {"samples": self.samples, "ticks": self.ticks, "busy_s": self.busy_s,
+                "samples_per_s": self.samples / self.busy_s if self.busy_s > 0 else None,
+                "latency_p50_s": float(np.percentile(lat, 50)) if lat else None,
+                "latency_p99_s": float(np.percentile(lat, 99)) if lat else None,
+                "queue_wait_p50_s": float(np.percentile(waits, 50)) if waits else None,
+                "jobs_finished": len(self.finished)}
