@@ -62,6 +62,16 @@ def test_planner_matches_oracle(lib, Lx, two_W):
     assert np.array_equal(binding.plan(p), _oracle_ops_as_abi(lad, n_steps))
 
 
+def test_planner_matches_oracle_on_every_small_ladder(lib):
+    """Every ladder shape up to Lx = 10 (all even cluster sizes), two steps."""
+    for Lx in range(1, 11):
+        for two_W in range(0, 2 * Lx + 1, 2):
+            p = binding.params(Lx, two_W, beta=0.2, tau=0.05)
+            lad = model.Ladder(Lx, two_W)
+            assert np.array_equal(binding.plan(p), _oracle_ops_as_abi(lad, 2)), (Lx, two_W)
+            assert binding.num_env(p) == len(lad.env)
+
+
 def test_planner_beta_zero_is_empty(lib):
     assert len(binding.plan(binding.params(4, 4, beta=0.0))) == 0
 
