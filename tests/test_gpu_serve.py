@@ -15,11 +15,11 @@ def test_served_jobs_equal_jobs_served_alone():
     from paper_1910_09142_gb300 import serve
 
     def p(Lx, two_W, cid, chi):
-        return b.params(Lx, two_W, J_rung=0.7, beta=0.4, tau=0.1, chi_max=chi, cutoff=1e-10, seed=9,
+        return b.params(Lx, two_W, J_rung=0.7, beta=0.2, tau=0.1, chi_max=chi, cutoff=1e-10, seed=9,
                         chain_id=cid)
 
-    arrivals = [(0, p(3, 2, 1, 32), 3, 1), (1, p(4, 4, 2, 32), 2, 0), (1, p(2, 0, 3, 16), 4, 1),
-                (3, p(3, 2, 4, 32), 1, 0)]
+    arrivals = [(0, p(3, 2, 1, 16), 3, 1), (1, p(3, 4, 2, 16), 2, 0), (1, p(2, 0, 3, 16), 4, 1),
+                (3, p(3, 2, 4, 16), 1, 0)]
     arena = 1 << 30
     ctx = b.Context(arena)
     try:
