@@ -68,3 +68,12 @@ def test_reference_arm_is_silent_on_other_ranks(capsys, monkeypatch):
 
 
 pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def test_oracle_baseline_pool_uses_every_requested_core():
+    """bench.oracle_parallel: one oracle chain per spawned process, 1 BLAS thread each."""
+    import bench
+    cfg = dict(Lx=2, two_W=2, J_leg=1.0, J_rung=1.0, beta=0.2, tau=0.1, chi_max=8, cutoff=1e-10)
+    rate, per_step, procs, wall = bench.oracle_parallel(2, procs=2, cfg=cfg)
+    assert procs == 2 and len(per_step) == 2 and rate > 0 and wall > 0
+    assert abs(rate - 4 / sum(per_step)) < 1e-12
