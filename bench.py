@@ -109,7 +109,11 @@ def oracle_parallel(steps, procs=None, cfg=None):
     on `procs` host cores (default: all).  Processes are started with spawn so
     that no CUDA state is forked.  Returns (samples/s, per-step wall times, procs)."""
     import multiprocessing as mp
-    procs = procs or os.cpu_count() or 1
+    if not procs:
+        try:
+            procs = len(os.sched_getaffinity(0))      # the cores this process may run on
+        except (AttributeError, OSError):
+            procs = os.cpu_count() or 1
     cfg = cfg or synth.ladder("ladder16")
     ctx = mp.get_context("spawn")
     # children read the BLAS thread count when they first import numpy, which
