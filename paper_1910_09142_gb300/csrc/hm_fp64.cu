@@ -430,25 +430,6 @@ __device__ void cta_transfer(const double* Ein, const double* A, int cl, int cr,
   cta_gemm<true, false>(cr, cr, 3 * cl, 1.0, A, cr, Z, cr, 0.0, Eout, cr, sh.g);
 }
 
-// Tr[sum_{s,t} O[s][t] A^{sT} E A^t] (right environment = identity).
-__device__ double cta_close(const double* E, const double* A, int cl, int cr, const double* O,
-                            double* Z, Shared& sh) {
-  if (threadIdx.x == 0) sh.scal[4] += 6.0 * cl * cl * cr + 2.0 * 9.0 * cl * cr;
-  cta_gemm<false, false>(cl, 3 * cr, cl, 1.0, E, cl, A, 3 * cr, 0.0, Z, 3 * cr, sh.g);
-  double acc = 0.0;
-  for (int e = threadIdx.x; e < cl * cr; e += NT) {
-    const int i = e / cr, r = e % cr;
-    const double* z = Z + (size_t)i * 3 * cr + r;
-    const double* a = A + (size_t)i * 3 * cr + r;
-    const double z0 = z[0], z1 = z[cr], z2 = z[2 * cr];
-    acc += a[0] * (O[0] * z0 + O[1] * z1 + O[2] * z2) + a[cr] * (O[3] * z0 + O[4] * z1 + O[5] * z2) +
-           a[2 * cr] * (O[6] * z0 + O[7] * z1 + O[8] * z2);
-  }
-  double d1 = 0.0, d2 = 0.0;
-  block_sum3(acc, d1, d2, sh);
-  return acc;
-}
-
 __device__ __constant__ double kSz[9] = {1, 0, 0, 0, 0, 0, 0, 0, -1};
 // S+ = sqrt(2) (|+1><0| + |0><-1|); S- its transpose (basis m = +1, 0, -1)
 __device__ __constant__ double kSp[9] = {0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0, 0, 0};
