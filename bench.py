@@ -36,7 +36,7 @@ METRIC = "hybrid-METTS samples/s (Lx=16 ladder, chi=256)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)    # one step is ~70 s of GPU time (256 samples)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -62,7 +62,7 @@ def workload(args):
     return cfg
 
 
-def workload_config(args, chains):
+def workload_config(args, chains, bytes_per_chain=None):
     cfg = workload(args)
     return {"workload": "S=1 Heisenberg ladder Lx=%d x 2, 2W=%d cluster sites, beta=%g, tau=%g, "
                         "chi_max=%d, cutoff=%g, %d chains/GPU" % (cfg["Lx"], cfg["two_W"], cfg["beta"], cfg["tau"],
@@ -70,7 +70,8 @@ def workload_config(args, chains):
             "Lx": cfg["Lx"], "two_W": cfg["two_W"], "beta": cfg["beta"], "tau": cfg["tau"],
             "chi_max": cfg["chi_max"], "cutoff": cfg["cutoff"], "J_leg": cfg["J_leg"],
             "J_rung": cfg["J_rung"], "chains_per_gpu": chains, "precision": args.precision,
-            "l2": "inputs larger than L2 (chain states ~%.0f GB resident)" % (chains * 0.075),
+            "l2": "inputs larger than L2 (%s of chain state resident)" % (
+                "%.1f GB" % (chains * bytes_per_chain / 1e9) if bytes_per_chain else "GBs"),
             "parallelism": "independent chains per GPU" if args.gpus > 1 else "1 GPU"}
 
 
@@ -278,7 +279,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
-        e2e_steps = max(1, min(args.steps, 2))
+        e2e_steps = 1
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             ctx.evolve(ids)
@@ -302,7 +303,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == b.HM_MIXED else "f64", "data": "synthetic",
-            "config": workload_config(args, n),
+            "config": workload_config(args, n, per),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "note": "per-sample latency = step time (all chains of a step finish together)"},
             "roofline": {"bound": "alu", "kernel": "evolve (two-site ops)", "achieved": achieved, "peak": peak,
