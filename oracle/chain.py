@@ -20,13 +20,12 @@ from . import model, mps as mpsmod, measure as measmod, collapse as colmod
 class HybridChain:
     def __init__(self, Lx, two_W, J_leg=1.0, J_rung=1.0, beta=1.0, tau=0.05,
                  chi_max=64, cutoff=1e-12, seed=0, chain_id=0,
-                 basis_zx=True, meas_cols=None):
+                 basis_zx=True, meas_cols=None, schedule=model.SCHEDULE_PLAIN):
         self.ladder = model.Ladder(Lx, two_W, J_leg, J_rung)
         self.beta, self.chi_max, self.cutoff = beta, chi_max, cutoff
         self.seed, self.chain_id, self.basis_zx = seed, chain_id, basis_zx
         self.n_steps, self.tau_eff = model.trotter_steps(beta, tau)
-        self.gates = model.gate_table(self.ladder, self.tau_eff)
-        self.ops = model.plan_ops(self.ladder, self.n_steps)
+        self.ops, self.gates = model.schedule(self.ladder, self.n_steps, self.tau_eff, schedule)
         if meas_cols is None:
             self.meas_bonds = self.ladder.measured_bonds()
         else:

@@ -19,7 +19,9 @@ implement exactly these, independently):
   immediately followed by its ancilla;
 * bonds sorted by (lower MPS index, upper MPS index); one second-order step is
   the forward sweep over that list with exp(-(tau/2) J h) followed by the
-  reversed sweep with the same gates; consecutive half steps are not merged;
+  reversed sweep with the same gates; in the plain schedule consecutive half
+  steps are not merged (the fused schedule, ``fuse_ops``, merges every run of
+  splits on one site pair, half-step turning points included);
 * a gate on MPS sites i<j is applied with swap gates.  In a forward half step
   the centre is brought to i, site i is swapped right up to j-1, the gate acts
   on (j-1, j) and the site is swapped back; in a reverse half step the mirror
@@ -210,3 +212,87 @@ def plan_ops(ladder, n_steps):
         ops.append((MOVE_L, c, -1, -1))
         c -= 1
     return ops
+
+
+SCHEDULE_PLAIN = "plain"   # the op list of plan_ops as it stands
+SCHEDULE_FUSED = "fused"   # plan_ops followed by fuse_ops
+
+
+def _centre_after(op, c):
+    kind, k, _, absorb = op
+    if kind == SPLIT:
+        return k if absorb == ABSORB_L else k + 1
+    return k + 1 if kind == MOVE_R else k - 1
+
+
+def fuse_ops(ops, gates):
+    """Merge consecutive truncated splits that act on the same pair of sites.
+
+    Sec. I.A applies a product of two-site gates; Sec. II's second-order
+    step is palindromic.  Two gates applied one after the other to the same
+    MPS pair (k, k+1) are one gate, their matrix product: the reverse sweep's
+    first bond meets the forward sweep's last one (exp(-(tau/2)J h) twice =
+    exp(-tau J h), the merged half steps of a second-order product), and a
+    bond gate meets the SWAP that starts or ends a neighbouring bond's swap
+    path.  A SWAP followed by a SWAP on the same pair is the identity; both
+    drop out.  If they moved the centre, an exact move takes their place.
+    The evolved state is the same product of gates applied to the same state,
+    so without truncation it is unchanged.  With truncation, one SVD
+    replaces two or more.
+
+    ``ops`` come from ``plan_ops`` and ``gates`` from ``gate_table``.
+    Returns ``(ops, gates)``.  New gate entries hold the products and are
+    appended in order of first use.  A fused op keeps the absorb side of the
+    last op it replaces.
+    """
+    # stack entries: [op, centre before it, word of base gate indices]
+    out = []
+    c = 0
+    for op in ops:
+        kind, k, g, absorb = op
+        c_next = _centre_after(op, c)
+        top = out[-1] if out else None
+        if kind == SPLIT and top is not None and top[0][0] == SPLIT and top[0][1] == k:
+            out.pop()
+            word = top[2] + [g]
+            if len(word) >= 2 and word[-1] == GATE_SWAP and word[-2] == GATE_SWAP:
+                word = word[:-2]
+            if word:
+                out.append([(SPLIT, k, None, absorb), top[1], word])
+            elif top[1] != c_next:
+                move = MOVE_R if c_next > top[1] else MOVE_L
+                out.append([(move, top[1], -1, -1), top[1], None])
+            c = c_next
+            continue
+        out.append([op, c, [g] if kind == SPLIT else None])
+        c = c_next
+    table = list(gates)
+    index = {}
+    fused = []
+    for op, _, word in out:
+        if op[0] != SPLIT:
+            fused.append(op)
+            continue
+        if len(word) == 1:
+            gi = word[0]
+        else:
+            key = tuple(word)
+            if key not in index:
+                m = gates[word[0]]
+                for w in word[1:]:
+                    m = gates[w] @ m
+                index[key] = len(table)
+                table.append(m)
+            gi = index[key]
+        fused.append((SPLIT, op[1], gi, op[3]))
+    return fused, table
+
+
+def schedule(ladder, n_steps, tau_eff, kind=SCHEDULE_PLAIN):
+    """Op list and gate table of one evolution by beta/2, plain or fused."""
+    ops, gates = plan_ops(ladder, n_steps), gate_table(ladder, tau_eff)
+    if kind == SCHEDULE_FUSED:
+        return fuse_ops(ops, gates)
+    if kind != SCHEDULE_PLAIN:
+        raise ValueError("unknown schedule %r" % (kind,))
+    return ops, gates

@@ -23,6 +23,9 @@ HM_FP64 = 0
 HM_MIXED = 1
 HM_ZX_ALTERNATE = 0
 HM_Z_ONLY = 1
+HM_SCHED_PLAIN = 0
+HM_SCHED_FUSED = 1
+SCHEDULES = {"plain": HM_SCHED_PLAIN, "fused": HM_SCHED_FUSED}
 
 _ERRNAMES = {HM_ERR_ARG: "HM_ERR_ARG", HM_ERR_NOMEM: "HM_ERR_NOMEM", HM_ERR_CUDA: "HM_ERR_CUDA",
              HM_ERR_NUMERIC: "HM_ERR_NUMERIC", HM_ERR_TIMEOUT: "HM_ERR_TIMEOUT",
@@ -49,14 +52,17 @@ class Params(ctypes.Structure):
                 ("chi_max", ctypes.c_int32), ("cutoff", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("chain_id", ctypes.c_uint32), ("basis_schedule", ctypes.c_int32),
-                ("meas_col_lo", ctypes.c_int32), ("meas_col_hi", ctypes.c_int32)]
+                ("meas_col_lo", ctypes.c_int32), ("meas_col_hi", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 def params(Lx, two_W, J_leg=1.0, J_rung=1.0, beta=1.0, tau=0.05, chi_max=64, cutoff=1e-12,
-           precision=HM_FP64, seed=0, chain_id=0, basis_zx=True, meas_cols=None):
+           precision=HM_FP64, seed=0, chain_id=0, basis_zx=True, meas_cols=None, schedule="plain"):
+    """``schedule``: "plain" / "fused" or HM_SCHED_PLAIN / HM_SCHED_FUSED."""
     lo, hi = (-1, -1) if meas_cols is None else meas_cols
+    sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     return Params(Lx, two_W, J_leg, J_rung, beta, tau, chi_max, cutoff, precision, seed, chain_id,
-                  HM_ZX_ALTERNATE if basis_zx else HM_Z_ONLY, lo, hi)
+                  HM_ZX_ALTERNATE if basis_zx else HM_Z_ONLY, lo, hi, sched)
 
 
 _lib = None

@@ -49,6 +49,7 @@ struct Layout {
   std::vector<int32_t> region;        // physical sites of the measured columns, sorted
   int n_steps = 0;
   double tau_eff = 0.0;
+  bool fused = false;                 // HM_SCHED_FUSED
 };
 
 int check_params(const hm_params* p, std::string* err) {
@@ -65,6 +66,8 @@ int check_params(const hm_params* p, std::string* err) {
     return fail(err, HM_ERR_ARG, "unsupported precision %d", p->precision);
   if (p->basis_schedule != HM_ZX_ALTERNATE && p->basis_schedule != HM_Z_ONLY)
     return fail(err, HM_ERR_ARG, "unknown basis schedule");
+  if (p->schedule != HM_SCHED_PLAIN && p->schedule != HM_SCHED_FUSED)
+    return fail(err, HM_ERR_ARG, "unknown op schedule %d", p->schedule);
   const bool dflt = p->meas_col_lo == -1 && p->meas_col_hi == -1;
   if (!dflt && (p->meas_col_lo < 0 || p->meas_col_hi > p->Lx || p->meas_col_lo >= p->meas_col_hi))
     return fail(err, HM_ERR_ARG, "measured columns must satisfy 0 <= lo < hi <= Lx");
@@ -124,6 +127,7 @@ Layout make_layout(const hm_params& p) {
     L.n_steps = std::max(1, (int)std::floor(p.beta / (2.0 * p.tau) + 0.5));
     L.tau_eff = p.beta / (2.0 * L.n_steps);
   }
+  L.fused = p.schedule == HM_SCHED_FUSED;
   return L;
 }
 
@@ -219,6 +223,89 @@ std::vector<double> gate_table(const Layout& L) {
   return g;
 }
 
+// Ops plus the gate table they index (entries of gate_table first).
+struct Schedule {
+  std::vector<OpDev> ops;
+  std::vector<double> gates;          // n_gates * 81
+  int32_t n_gates() const { return (int32_t)(gates.size() / 81); }
+};
+
+// HM_SCHED_FUSED: one pass over the plain op list with a stack.  A
+// truncating split on the pair (k, k+1) that directly follows another
+// truncating split on the same pair is folded into it: the gate word grows by
+// one letter, and the absorb side becomes the later op's.  Two SWAPs at the
+// end of a word annihilate.  When a word empties, its ops vanish; an exact
+// centre move replaces them if they had moved the centre.  The folded op can
+// then fold into the op below it on the stack.  Each word of two or more
+// letters becomes a gate table entry holding the product, the later letters
+// on the left.  The gates act on the physical legs only (Sec. I.A), so the
+// product of gates on one pair is itself a two-site gate; the state without
+// truncation is unchanged.
+void fuse_schedule(Schedule& s) {
+  struct Item {
+    OpDev op;
+    int c0;                           // centre before the op
+    std::vector<int32_t> word;        // gate letters, first applied first
+  };
+  std::vector<Item> st;
+  int c = 0;
+  for (const OpDev& op : s.ops) {
+    const int c1 = op.absorb ? op.k + 1 : op.k;
+    if (!op.exact && !st.empty() && !st.back().op.exact && st.back().op.k == op.k) {
+      Item it = std::move(st.back());
+      st.pop_back();
+      it.word.push_back(op.gate);
+      const size_t n = it.word.size();
+      if (n >= 2 && it.word[n - 1] == GATE_SWAP && it.word[n - 2] == GATE_SWAP) it.word.resize(n - 2);
+      if (!it.word.empty()) {
+        it.op.absorb = op.absorb;
+        st.push_back(std::move(it));
+      } else if (it.c0 != c1) {
+        st.push_back({{op.k, GATE_ID, c1 == op.k + 1 ? 1 : 0, 1}, it.c0, {GATE_ID}});
+      }
+      c = c1;
+      continue;
+    }
+    st.push_back({op, c, {op.gate}});
+    c = c1;
+  }
+  std::map<std::vector<int32_t>, int32_t> entry;
+  std::vector<OpDev> ops;
+  ops.reserve(st.size());
+  for (Item& it : st) {
+    if (it.word.size() > 1) {
+      auto f = entry.find(it.word);
+      if (f == entry.end()) {
+        double P[81], T[81];
+        std::memcpy(P, &s.gates[(size_t)it.word[0] * 81], sizeof P);
+        for (size_t q = 1; q < it.word.size(); ++q) {
+          const double* G = &s.gates[(size_t)it.word[q] * 81];
+          for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) {
+              double acc = 0.0;
+              for (int t = 0; t < 9; ++t) acc += G[i * 9 + t] * P[t * 9 + j];
+              T[i * 9 + j] = acc;
+            }
+          std::memcpy(P, T, sizeof P);
+        }
+        f = entry.emplace(it.word, s.n_gates()).first;
+        s.gates.insert(s.gates.end(), P, P + 81);
+      }
+      it.op.gate = f->second;
+    } else {
+      it.op.gate = it.word[0];
+    }
+    ops.push_back(it.op);
+  }
+  s.ops.swap(ops);
+}
+
+Schedule make_schedule(const Layout& L) {
+  Schedule s{plan(L), gate_table(L)};
+  if (L.fused) fuse_schedule(s);
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // Memory plan of one chain (all inside one arena block).
 // ---------------------------------------------------------------------------
@@ -235,7 +322,7 @@ struct MemPlan {
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops) {
+MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gates) {
   MemPlan m;
   const int n = L.n_sites;
   m.bmax.resize(n + 1);
@@ -271,7 +358,7 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops) {
   };
   m.off_desc = take(sizeof(ChainDev));
   m.off_ops = take(std::max<size_t>(n_ops, 1) * sizeof(OpDev));
-  m.off_gates = take(81 * sizeof(double) * (GATE_BOND0 + L.bonds.size()));
+  m.off_gates = take(81 * sizeof(double) * n_gates);
   m.off_kind = take(n * sizeof(int32_t));
   m.off_mi = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
   m.off_mj = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
@@ -481,8 +568,8 @@ int hm_query_memory(const hm_params* p, size_t* bytes_out) {
   if (rc) return rc;
   if (!bytes_out) return fail(nullptr, HM_ERR_ARG, "null output");
   const Layout L = make_layout(*p);
-  const std::vector<OpDev> ops = plan(L);
-  *bytes_out = mem_plan(*p, L, ops.size()).total;
+  const Schedule sc = make_schedule(L);
+  *bytes_out = mem_plan(*p, L, sc.ops.size(), sc.gates.size() / 81).total;
   return HM_OK;
 }
 
@@ -506,7 +593,7 @@ int hm_plan(const hm_params* p, int32_t* ops, int32_t cap, int32_t* n_ops_out) {
   int rc = check_params(p, nullptr);
   if (rc) return rc;
   if (!n_ops_out) return fail(nullptr, HM_ERR_ARG, "null output");
-  const std::vector<OpDev> v = plan(make_layout(*p));
+  const std::vector<OpDev> v = make_schedule(make_layout(*p)).ops;
   *n_ops_out = (int32_t)v.size();
   if (ops) {
     if (cap < (int32_t)v.size()) return fail(nullptr, HM_ERR_ARG, "op buffer too small (%zu ops)", v.size());
@@ -524,7 +611,7 @@ int hm_gates(const hm_params* p, double* out, int32_t cap, int32_t* n_gates_out)
   int rc = check_params(p, nullptr);
   if (rc) return rc;
   if (!n_gates_out) return fail(nullptr, HM_ERR_ARG, "null output");
-  const std::vector<double> g = gate_table(make_layout(*p));
+  const std::vector<double> g = make_schedule(make_layout(*p)).gates;
   *n_gates_out = (int32_t)(g.size() / 81);
   if (out) {
     if ((size_t)cap * 81 < g.size()) return fail(nullptr, HM_ERR_ARG, "gate buffer too small");
@@ -542,8 +629,9 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   Chain* ch = new Chain;
   ch->p = *p;
   ch->L = make_layout(*p);
-  ch->ops = plan(ch->L);
-  ch->mp = mem_plan(*p, ch->L, ch->ops.size());
+  Schedule sched = make_schedule(ch->L);
+  ch->ops = std::move(sched.ops);
+  ch->mp = mem_plan(*p, ch->L, ch->ops.size(), sched.gates.size() / 81);
   ch->n_obs = 1 + 2 * (int)ch->L.meas.size();
   {
     // at most 8 measured bonds may start on one site (measure kernel buffer)
@@ -576,7 +664,7 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   d.chi_max = p->chi_max;
   d.n_env = L.n_env;
   d.n_meas = (int32_t)L.meas.size();
-  d.n_gates = (int32_t)(GATE_BOND0 + L.bonds.size());
+  d.n_gates = sched.n_gates();
   d.basis_zx = p->basis_schedule == HM_ZX_ALTERNATE;
   d.first_cluster = L.first_cluster;
   d.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
@@ -612,8 +700,7 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   d.chi_cap = mp.chi_cap;
   std::memcpy(img.data() + mp.off_desc, &d, sizeof d);
   if (!ch->ops.empty()) std::memcpy(img.data() + mp.off_ops, ch->ops.data(), ch->ops.size() * sizeof(OpDev));
-  const std::vector<double> g = gate_table(L);
-  std::memcpy(img.data() + mp.off_gates, g.data(), g.size() * sizeof(double));
+  std::memcpy(img.data() + mp.off_gates, sched.gates.data(), sched.gates.size() * sizeof(double));
   std::memcpy(img.data() + mp.off_kind, L.kind.data(), L.kind.size() * sizeof(int32_t));
   std::vector<int> ends;
   for (size_t q = 0; q < L.meas.size(); ++q) {

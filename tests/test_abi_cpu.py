@@ -72,6 +72,51 @@ def test_planner_matches_oracle_on_every_small_ladder(lib):
             assert binding.num_env(p) == len(lad.env)
 
 
+def _oracle_fused(lad, n_steps, tau_eff):
+    ops, gates = model.schedule(lad, n_steps, tau_eff, model.SCHEDULE_FUSED)
+    out = []
+    for kind, k, g, absorb in ops:
+        if kind == model.SPLIT:
+            out.append((k, g + 1, absorb, 0))          # oracle 0 = SWAP; library 0 = identity
+        elif kind == model.MOVE_R:
+            out.append((k, 0, 1, 1))
+        else:
+            out.append((k - 1, 0, 0, 1))
+    return np.array(out, dtype=np.int32).reshape(-1, 4), gates
+
+
+@pytest.mark.parametrize("Lx,two_W", CASES)
+def test_fused_planner_matches_oracle(lib, Lx, two_W):
+    """HM_SCHED_FUSED: same ops, same product gates (built independently)."""
+    lad = model.Ladder(Lx, two_W, 1.0, 0.7)
+    n_steps, teff = model.trotter_steps(0.6, 0.1)
+    p = binding.params(Lx, two_W, J_rung=0.7, beta=0.6, tau=0.1, schedule="fused")
+    ref_ops, ref_gates = _oracle_fused(lad, n_steps, teff)
+    assert np.array_equal(binding.plan(p), ref_ops)
+    cg = binding.gates(p)
+    assert len(cg) == len(ref_gates) + 1
+    for i, g in enumerate(ref_gates):
+        assert np.abs(cg[1 + i] - g).max() < 1e-14, i
+    plain = binding.plan(binding.params(Lx, two_W, J_rung=0.7, beta=0.6, tau=0.1))
+    assert len(ref_ops) < len(plain) or Lx == 1
+
+
+def test_fused_planner_on_every_small_ladder(lib):
+    for Lx in range(1, 9):
+        for two_W in range(0, 2 * Lx + 1, 2):
+            lad = model.Ladder(Lx, two_W)
+            p = binding.params(Lx, two_W, beta=0.2, tau=0.05, schedule=binding.HM_SCHED_FUSED)
+            assert np.array_equal(binding.plan(p), _oracle_fused(lad, 2, 0.05)[0]), (Lx, two_W)
+
+
+def test_fused_schedule_memory(lib):
+    # 479 fewer 16-byte ops, 17 more 648-byte product gates: same size to 64 KB
+    base = dict(Lx=16, two_W=8, chi_max=256, beta=1.0, tau=0.05)
+    plain = binding.query_memory(binding.params(**base))
+    fused = binding.query_memory(binding.params(**base, schedule="fused"))
+    assert abs(plain - fused) < 64 << 10
+
+
 def test_planner_beta_zero_is_empty(lib):
     assert len(binding.plan(binding.params(4, 4, beta=0.0))) == 0
 
@@ -110,7 +155,7 @@ def test_memory_query_scales_with_chi(lib):
 @pytest.mark.parametrize("kw", [dict(Lx=0, two_W=0), dict(Lx=4, two_W=3), dict(Lx=4, two_W=10),
                                 dict(Lx=4, two_W=4, tau=0.0), dict(Lx=4, two_W=4, chi_max=0),
                                 dict(Lx=4, two_W=4, cutoff=1.5), dict(Lx=4, two_W=4, beta=-1.0),
-                                dict(Lx=4, two_W=4, meas_cols=(3, 2))])
+                                dict(Lx=4, two_W=4, meas_cols=(3, 2)), dict(Lx=4, two_W=4, schedule=2)])
 def test_invalid_parameters_rejected(lib, kw):
     with pytest.raises(binding.HmError) as e:
         binding.num_obs(binding.params(**kw))

@@ -1,0 +1,99 @@
+"""HM_SCHED_FUSED on the GPU vs the oracle's fused schedule (GPU tests).
+
+The fused schedule only changes the op list and the gate table the kernels
+read, so it is held to the bars of the plain one. FP64: states at 1e-10,
+per-sample observables at 1e-10 relative, collapse outcomes bit-exact and
+log-probabilities at 1e-9. Mixed: the stated 1e-3 / 2e-3. Without
+truncation the fused and the plain evolution reach the same state.
+"""
+import numpy as np
+import pytest
+
+from oracle import chain as ochain
+from oracle import mps as omps
+
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL = 1e-10, 1e-12
+
+CFGS = [
+    dict(Lx=3, two_W=2, J_leg=1.0, J_rung=0.5, beta=0.6, tau=0.1, chi_max=64, cutoff=1e-12),
+    dict(Lx=3, two_W=0, J_leg=1.0, J_rung=0.7, beta=1.2, tau=0.1, chi_max=64, cutoff=1e-12),
+    dict(Lx=5, two_W=2, J_leg=1.0, J_rung=1.0, beta=0.8, tau=0.1, chi_max=12, cutoff=1e-8),
+    dict(Lx=4, two_W=4, J_leg=1.0, J_rung=1.0, beta=2.0, tau=0.1, chi_max=64, cutoff=1e-12),
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_1910_09142_gb300 import binding
+    assert torch.cuda.is_available()
+    c = binding.Context(2 << 30)
+    yield c
+    c.close()
+
+
+def _b():
+    from paper_1910_09142_gb300 import binding
+    return binding
+
+
+def _same_state(a, b, tol=1e-10):
+    va, vb = omps.MPS(a).to_dense(), omps.MPS(b).to_dense()
+    return np.abs(va - np.sign(va @ vb) * vb).max() < tol
+
+
+def test_fused_samples_match_oracle(ctx):
+    """Three Markov steps of every config, fused and plain chains in one batch."""
+    b = _b()
+    ps = [b.params(**cfg, seed=5, chain_id=1, schedule="fused") for cfg in CFGS]
+    ps.append(b.params(**CFGS[0], seed=5, chain_id=1))                     # plain, same batch
+    ids = [ctx.init_chain(p) for p in ps]
+    refs = [ochain.HybridChain(seed=5, chain_id=1, schedule="fused", **cfg) for cfg in CFGS]
+    refs.append(ochain.HybridChain(seed=5, chain_id=1, **CFGS[0]))
+    try:
+        for step in range(3):
+            ctx.evolve(ids)
+            if step == 0:
+                for cid, ref in zip(ids, refs):
+                    assert _same_state(ctx.get_mps(cid), ref.evolve().tensors)
+            for cid, p, ref in zip(ids, ps, refs):
+                obs = ctx.measure([cid], b.num_obs(p))[0]
+                env, logp = ctx.collapse([cid], b.num_env(p))
+                r = ref.sample()
+                assert np.allclose(obs, r["obs"], rtol=RTOL, atol=ATOL), (obs, r["obs"])
+                assert list(env[0]) == r["env_out"]
+                assert abs(logp[0] - r["logp"]) < 1e-9
+    finally:
+        for cid in ids:
+            ctx.free_chain(cid)
+
+
+def test_fused_equals_plain_without_truncation(ctx):
+    b = _b()
+    cfg = dict(Lx=3, two_W=2, J_leg=1.0, J_rung=0.5, beta=0.6, tau=0.1, chi_max=729, cutoff=0.0)
+    ids = [ctx.init_chain(b.params(**cfg, seed=2, schedule=s)) for s in ("plain", "fused")]
+    try:
+        ctx.evolve(ids)
+        assert _same_state(ctx.get_mps(ids[0]), ctx.get_mps(ids[1]))
+    finally:
+        for cid in ids:
+            ctx.free_chain(cid)
+
+
+def test_fused_mixed_within_stated_tolerance(ctx):
+    b = _b()
+    cfg = CFGS[3]
+    p = b.params(**cfg, seed=0, chain_id=0, precision=b.HM_MIXED, schedule="fused")
+    cid = ctx.init_chain(p)
+    ref = ochain.HybridChain(seed=0, chain_id=0, schedule="fused", **cfg)
+    try:
+        ctx.evolve([cid])
+        obs = ctx.measure([cid], b.num_obs(p))[0]
+        r = ref.sample()
+        assert abs(obs[0] - r["obs"][0]) < 1e-3 * abs(r["obs"][0])
+        assert np.abs(obs[1:] - r["obs"][1:]).max() < 2e-3
+        ctx.collapse([cid], b.num_env(p))
+    finally:
+        ctx.free_chain(cid)
