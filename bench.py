@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--chains", type=int, default=256)
+    ap.add_argument("--schedule", default="plain", choices=["plain", "fused"],
+                    help="op schedule: plain, or fused (runs of splits on one site pair folded into one)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # workload overrides (smaller cases for profiling; not the headline line)
@@ -59,6 +61,7 @@ def workload(args):
     for key, val in (("Lx", args.Lx), ("two_W", args.two_W), ("beta", args.beta), ("chi_max", args.chi_max)):
         if val is not None:
             cfg[key] = val
+    cfg["schedule"] = getattr(args, "schedule", "plain")
     return cfg
 
 
@@ -70,6 +73,7 @@ def workload_config(args, chains, bytes_per_chain=None):
             "Lx": cfg["Lx"], "two_W": cfg["two_W"], "beta": cfg["beta"], "tau": cfg["tau"],
             "chi_max": cfg["chi_max"], "cutoff": cfg["cutoff"], "J_leg": cfg["J_leg"],
             "J_rung": cfg["J_rung"], "chains_per_gpu": chains, "precision": args.precision,
+            "schedule": cfg["schedule"],
             "l2": "inputs larger than L2 (%s of chain state resident)" % (
                 "%.1f GB" % (chains * bytes_per_chain / 1e9) if bytes_per_chain else "GBs"),
             "parallelism": "independent chains per GPU" if args.gpus > 1 else "1 GPU"}

@@ -192,3 +192,20 @@ def test_fused_op_count_lx16():
 def test_unknown_schedule_rejected():
     with pytest.raises(ValueError):
         model.schedule(model.Ladder(2, 2), 1, 0.1, "merged")
+
+
+def test_observables_stable_under_gate_rounding_at_the_chi_cap():
+    """Lx=4, 2W=4, beta=2, chi=64: about 300 fused splits cut at the chi cap.
+    A 1e-16 relative change of every gate leaves the observables within
+    1e-12 relative (the 1e-10 parity bar holds), although the dense state
+    itself may move far more (the cut falls between close singular values)."""
+    from oracle import chain, measure
+    cfg = dict(Lx=4, two_W=4, J_leg=1.0, J_rung=1.0, beta=2.0, tau=0.1, chi_max=64, cutoff=1e-12)
+    ch = chain.HybridChain(seed=5, chain_id=1, schedule=model.SCHEDULE_FUSED, **cfg)
+    log = []
+    ref = measure.measure(mps.evolve(ch.initial_mps(), ch.ops, ch.gates, 64, 1e-12, log), ch.meas_bonds)
+    assert sum(1 for r in log if r[5] == 64) > 200
+    rng = np.random.default_rng(0)
+    g2 = [g * (1 + 1e-16 * rng.standard_normal(g.shape)) for g in ch.gates]
+    obs = measure.measure(mps.evolve(ch.initial_mps(), ch.ops, g2, 64, 1e-12), ch.meas_bonds)
+    assert np.max(np.abs(obs - ref) / np.maximum(np.abs(ref), 1e-2)) < 1e-12
