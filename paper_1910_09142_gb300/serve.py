@@ -24,12 +24,13 @@ import time
 import numpy as np
 
 from . import binding
+from .estimators import Estimator
 
 
 class Job:
     """One sampling request; ``results`` gets one observable vector per kept sample."""
 
-    def __init__(self, job_id, params, n_samples, n_warmup=0, arrival=None):
+    def __init__(self, job_id, params, n_samples, n_warmup=0, arrival=None, bin_size=10):
         self.id = job_id
         self.params = params                 # binding.Params
         self.n_samples = int(n_samples)
@@ -43,6 +44,16 @@ class Job:
         self.env = []                        # collapse outcomes of every step
         self.latencies = []                  # seconds per kept sample
         self.bytes = 0
+        self.bin_size = int(bin_size)
+        self.estimator = None                # Estimator over the kept samples
+
+    def estimate(self):
+        """Mean of every observable over the kept samples, and its binned
+        standard error (None until two bins are complete)."""
+        if self.estimator is None or self.estimator.count == 0:
+            return None, None
+        err = self.estimator.stderr() if self.estimator.sums[5][0] >= 2 else None
+        return self.estimator.mean(), err
 
     @property
     def complete(self):
@@ -121,6 +132,9 @@ class Server:
         for j in self.active:
             if j.done_steps >= j.n_warmup:
                 j.results.append(obs[j.id])
+                if j.estimator is None:
+                    j.estimator = Estimator(len(obs[j.id]), j.bin_size)
+                j.estimator.add(j.id, obs[j.id])
                 j.latencies.append(dt)
                 self.samples += 1
             j.done_steps += 1

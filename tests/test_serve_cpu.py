@@ -124,3 +124,16 @@ def test_latency_statistics():
     st = srv.run([(0, _p(3, 1), 3, 0)])
     assert st["samples"] == 3 and st["latency_p50_s"] == pytest.approx(0.5)
     assert st["samples_per_s"] == pytest.approx(2.0)
+
+
+def test_job_estimate_over_kept_samples():
+    srv = serve.Server(FakeCtx(), 1 << 40)
+    job = srv.submit(_p(3, 4), 25, 3)
+    job.bin_size = 5
+    assert job.estimate() == (None, None)
+    srv.run()
+    mean, err = job.estimate()
+    x = np.array(job.results)
+    assert np.allclose(mean, x.mean(axis=0), atol=1e-12)
+    bins = x.reshape(5, 5, -1).mean(axis=1)
+    assert np.allclose(err, bins.std(axis=0, ddof=1) / np.sqrt(5), atol=1e-12)
