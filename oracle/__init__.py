@@ -20,6 +20,8 @@ Contents (each function cites the passage of the paper it follows):
                (Eq. sqrtrho) and a dense Trotterised state-vector evolver.
 * ``brute``    brute-force collapse enumeration and detailed balance
                (Sec. I.C.2) on tiny systems.
+* ``u1``       total-S^z block-sparse evolution with S^z-basis collapses
+               (Sec. II.C, Fig. qn).
 
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against
 closed forms, exact diagonalisation, library routines or brute force; see the
