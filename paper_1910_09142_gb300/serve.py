@@ -64,11 +64,12 @@ class Server:
     """FIFO admission by arena bytes and batch slots; one batched step per tick."""
 
     def __init__(self, ctx, arena_bytes, max_chains=448, clock=time.perf_counter,
-                 query_memory=None, num_obs=None, num_env=None):
+                 query_memory=None, num_obs=None, num_env=None, sleep=time.sleep):
         self.ctx = ctx
         self.capacity = int(arena_bytes)
         self.max_chains = int(max_chains)
         self.clock = clock
+        self.sleep = sleep
         self.query_memory = query_memory or binding.query_memory
         self.num_obs = num_obs or binding.num_obs
         self.num_env = num_env or binding.num_env
@@ -82,9 +83,10 @@ class Server:
         self._next_id = 0
 
     # -- requests ---------------------------------------------------------------------
-    def submit(self, params, n_samples, n_warmup=0):
-        """Queue a job; returns it.  ``params`` is a binding.Params."""
-        job = Job(self._next_id, params, n_samples, n_warmup, self.clock())
+    def submit(self, params, n_samples, n_warmup=0, arrival=None):
+        """Queue a job; returns it.  ``params`` is a binding.Params; ``arrival``
+        (clock time the request came in) defaults to now."""
+        job = Job(self._next_id, params, n_samples, n_warmup, self.clock() if arrival is None else arrival)
         job.bytes = self.query_memory(params)
         if job.bytes > self.capacity:
             raise ValueError("job %d needs %d bytes, more than the whole arena" % (job.id, job.bytes))
@@ -168,6 +170,32 @@ class Server:
                 return self.stats()
             tick += 1
 
+    def run_stream(self, requests, horizon_s=None):
+        """Serve a timed request stream.
+
+        ``requests``: iterable of (t_s, params, n_samples, n_warmup), t_s in
+        seconds after this call starts.  Each tick first submits every request
+        whose time has come (stamped with its arrival time, so the queueing
+        delay includes the wait for the tick boundary), then runs one step.
+        When nothing is resident or queued, the loop sleeps until the next
+        arrival.  It returns when everything has been served, or at the first
+        tick boundary after ``horizon_s``, leaving the rest queued or resident."""
+        pending = collections.deque(sorted(requests, key=lambda r: r[0]))
+        t0 = self.clock()
+        while True:
+            now = self.clock() - t0
+            if horizon_s is not None and now >= horizon_s:
+                return self.stats()
+            while pending and pending[0][0] <= now:
+                t, p, n, w = pending.popleft()
+                self.submit(p, n, w, arrival=t0 + t)
+            if not self.active and not self.queue:
+                if not pending:
+                    return self.stats()
+                self.sleep(pending[0][0] - now)
+                continue
+            self.step()
+
     # -- statistics ---------------------------------------------------------------------
     def stats(self):
         lat = [x for j in self.finished + self.active for x in j.latencies]
@@ -177,4 +205,6 @@ class Server:
                 "latency_p50_s": float(np.percentile(lat, 50)) if lat else None,
                 "latency_p99_s": float(np.percentile(lat, 99)) if lat else None,
                 "queue_wait_p50_s": float(np.percentile(waits, 50)) if waits else None,
-                "jobs_finished": len(self.finished)}
+                "queue_wait_p99_s": float(np.percentile(waits, 99)) if waits else None,
+                "jobs_finished": len(self.finished), "jobs_resident": len(self.active),
+                "jobs_queued": len(self.queue)}

@@ -46,3 +46,31 @@ def random_matrix(m, n, seed, decay=None):
 def env_draws(n_env, seed):
     """Seeded environment outcomes in {0, 1, 2} for explicit initial states."""
     return np.random.default_rng(seed).integers(0, 3, size=n_env).astype(np.int8)
+
+
+# Serving workload: a Poisson stream of sampling requests of mixed sizes.
+SERVE_MIX = dict(Lx=(8, 16, 32), two_W=(4, 8), beta=(0.5, 16.0), chi_max=(128, 256, 512),
+                 samples=(100, 2000), tau=0.05, cutoff=1e-7, J_leg=1.0, J_rung=1.0)
+
+
+def poisson_requests(rate, duration_s, seed, mix=None):
+    """Seeded request stream: exponential inter-arrival times of mean 1/rate
+    over [0, duration_s).  Each request draws Lx, two_W and chi_max uniformly
+    from the mix's choices, beta log-uniformly from its range, and the
+    sample count uniformly from its integer range.
+
+    Returns a list of (t_s, ladder parameter dict, n_samples)."""
+    mix = dict(SERVE_MIX if mix is None else mix)
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration_s:
+            return out
+        lo, hi = mix["beta"]
+        cfg = dict(Lx=int(rng.choice(mix["Lx"])), two_W=int(rng.choice(mix["two_W"])),
+                   beta=float(np.exp(rng.uniform(np.log(lo), np.log(hi)))), tau=mix["tau"],
+                   chi_max=int(rng.choice(mix["chi_max"])), cutoff=mix["cutoff"],
+                   J_leg=mix["J_leg"], J_rung=mix["J_rung"])
+        n = int(rng.integers(mix["samples"][0], mix["samples"][1] + 1))
+        out.append((t, cfg, n))

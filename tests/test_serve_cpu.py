@@ -137,3 +137,79 @@ def test_job_estimate_over_kept_samples():
     assert np.allclose(mean, x.mean(axis=0), atol=1e-12)
     bins = x.reshape(5, 5, -1).mean(axis=1)
     assert np.allclose(err, bins.std(axis=0, ddof=1) / np.sqrt(5), atol=1e-12)
+
+
+class _Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 0.0)
+
+
+class _TimedCtx(FakeCtx):
+    """Each batched evolve takes one second of the fake clock."""
+
+    def __init__(self, clock):
+        super().__init__()
+        self.clock = clock
+
+    def evolve(self, ids):
+        super().evolve(ids)
+        self.clock.t += 1.0
+
+
+def test_stream_admits_at_tick_boundaries_and_sleeps_when_idle():
+    clk = _Clock()
+    srv = serve.Server(_TimedCtx(clk), 1 << 40, clock=clk, sleep=clk.sleep)
+    reqs = [(2.0, _p(3, 1), 3, 0), (2.3, _p(4, 2), 1, 0), (9.5, _p(3, 3), 1, 1)]
+    st = srv.run_stream(reqs)
+    assert st["jobs_finished"] == 3 and st["samples"] == 5
+    a, b, c = sorted(srv.finished, key=lambda j: j.id)
+    assert a.admitted == pytest.approx(2.0)            # slept until the first arrival
+    assert b.admitted == pytest.approx(3.0)            # arrived mid-tick, joined at the next one
+    assert b.admitted - b.arrival == pytest.approx(0.7)
+    assert c.admitted == pytest.approx(9.5) and c.finished == pytest.approx(11.5)
+    assert st["queue_wait_p99_s"] == pytest.approx(0.7, abs=0.02)
+
+
+def test_stream_horizon_leaves_the_rest_resident_or_queued():
+    clk = _Clock()
+    srv = serve.Server(_TimedCtx(clk), 1 << 40, clock=clk, sleep=clk.sleep, max_chains=2)
+    reqs = [(0.0, _p(3, i), 10, 0) for i in range(5)]
+    st = srv.run_stream(reqs, horizon_s=3.5)
+    assert st["ticks"] == 4 and st["jobs_finished"] == 0
+    assert st["jobs_resident"] == 2 and st["jobs_queued"] == 3
+
+
+def test_poisson_request_stream():
+    import synth
+    r1 = synth.poisson_requests(50.0, 20.0, seed=3)
+    r2 = synth.poisson_requests(50.0, 20.0, seed=3)
+    assert [x[0] for x in r1] == [x[0] for x in r2]
+    assert abs(len(r1) - 1000) < 4 * np.sqrt(1000)                       # Poisson count
+    t = np.array([x[0] for x in r1])
+    assert np.all(np.diff(t) > 0) and t[-1] < 20.0
+    for _, cfg, n in r1:
+        assert cfg["Lx"] in (8, 16, 32) and cfg["two_W"] in (4, 8) and cfg["chi_max"] in (128, 256, 512)
+        assert 0.5 <= cfg["beta"] <= 16.0 and 100 <= n <= 2000
+        binding.params(**cfg)                                              # a valid chain
+    betas = np.array([c["beta"] for _, c, _ in r1])
+    assert abs(np.median(np.log(betas)) - 0.5 * (np.log(0.5) + np.log(16.0))) < 0.3   # log-uniform
+
+
+def test_poisson_stream_served_end_to_end():
+    import synth
+    mix = dict(synth.SERVE_MIX, Lx=(3, 4), two_W=(2, 4), chi_max=(16, 32), samples=(2, 6))
+    reqs = [(t, binding.params(**cfg, chain_id=i), n, 1)
+            for i, (t, cfg, n) in enumerate(synth.poisson_requests(2.0, 10.0, seed=1, mix=mix))]
+    clk = _Clock()
+    srv = serve.Server(_TimedCtx(clk), 1 << 40, clock=clk, sleep=clk.sleep)
+    st = srv.run_stream(reqs)
+    assert st["jobs_finished"] == len(reqs) and st["samples"] == sum(r[2] for r in reqs)
+    assert st["latency_p50_s"] == pytest.approx(1.0)
+    for job in srv.finished:
+        assert len(job.results) == job.n_samples and job.admitted >= job.arrival
