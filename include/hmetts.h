@@ -140,6 +140,19 @@ int hm_num_env(const hm_params* p, int32_t* n_env);
  * to draw them from the chain's Philox stream with sample index n = -1. */
 int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_chain* out);
 
+/* Resume a chain from its checkpoint (no counterpart in the paper; the
+ * state a chain carries between samples is only this, because step 4 resets
+ * the cluster to Bell pairs).  Allocates the chain like hm_init_chain and
+ * writes the initial state of sample `next_sample` (>= 1): env_out (host,
+ * n_env values in {0,1,2}) are the outcomes the collapse of sample
+ * next_sample - 1 returned, read in that sample's basis (Sz for an even
+ * index or under HM_Z_ONLY, Sx for an odd one).  The resumed chain then
+ * draws exactly what the uninterrupted chain would: same Philox counters,
+ * same bases.  Errors: HM_ERR_ARG for next_sample < 1 (use hm_init_chain),
+ * a NULL or out-of-range env_out, or any hm_init_chain error. */
+int hm_resume_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_out, int64_t next_sample,
+                    hm_chain* out);
+
 /* Release a chain's arena memory (synchronises the stream). */
 int hm_free_chain(hm_ctx* ctx, hm_chain chain);
 

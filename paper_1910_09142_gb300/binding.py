@@ -35,7 +35,7 @@ EXPORTS = ["hm_create", "hm_destroy", "hm_query_memory", "hm_num_obs", "hm_num_e
            "hm_free_chain", "hm_evolve", "hm_measure_cluster", "hm_measure_cluster_device",
            "hm_collapse", "hm_collapse_device", "hm_chain_stats", "hm_get_mps", "hm_set_mps",
            "hm_apply_ops", "hm_plan", "hm_gates", "hm_last_error", "hm_two_site_update_static",
-           "hm_measure_susceptibility"]
+           "hm_measure_susceptibility", "hm_resume_chain"]
 
 
 class HmError(RuntimeError):
@@ -86,6 +86,7 @@ def load(path=None):
         "hm_num_obs": [P(Params), P(i32)],
         "hm_num_env": [P(Params), P(i32)],
         "hm_init_chain": [vp, P(Params), vp, P(i64)],
+        "hm_resume_chain": [vp, P(Params), vp, i64, P(i64)],
         "hm_free_chain": [vp, i64],
         "hm_evolve": [vp, P(i64), i32],
         "hm_measure_cluster": [vp, P(i64), i32, vp, i32],
@@ -214,10 +215,17 @@ class Context:
     def _c(self, rc):
         _check(rc, self.h)
 
-    def init_chain(self, p, env_init=None):
+    def init_chain(self, p, env_init=None, next_sample=0):
+        """New chain (hm_init_chain), or with ``next_sample`` >= 1 a chain
+        resumed from its checkpoint (hm_resume_chain): ``env_init`` are then
+        the outcomes the collapse of sample next_sample - 1 returned."""
         out = ctypes.c_int64()
         env = None if env_init is None else np.ascontiguousarray(np.asarray(env_init, dtype=np.int8))
-        self._c(self.lib.hm_init_chain(self.h, ctypes.byref(p), _ptr(env), ctypes.byref(out)))
+        if next_sample:
+            self._c(self.lib.hm_resume_chain(self.h, ctypes.byref(p), _ptr(env), int(next_sample),
+                                             ctypes.byref(out)))
+        else:
+            self._c(self.lib.hm_init_chain(self.h, ctypes.byref(p), _ptr(env), ctypes.byref(out)))
         return out.value
 
     def free_chain(self, cid):

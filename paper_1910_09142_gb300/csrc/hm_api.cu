@@ -620,7 +620,10 @@ int hm_gates(const hm_params* p, double* out, int32_t cap, int32_t* n_gates_out)
   return HM_OK;
 }
 
-int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_chain* out) {
+// Allocation and first initial state of a chain; next_sample > 0 resumes a
+// checkpoint: the counters start at (n = next_sample, basis of sample n - 1).
+static int init_chain_impl(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, int64_t next_sample,
+                           hm_chain* out) {
   if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
   int rc = check_params(p, &ctx->err);
   if (rc) return rc;
@@ -722,6 +725,11 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   for (int s = 0; s < L.n_sites; ++s) ((double**)(img.data() + mp.off_siteptr))[s] = (double*)(base + mp.slot_off[s]);
   if (env_init)
     for (int e = 0; e < L.n_env; ++e) ((int32_t*)(img.data() + mp.off_env))[e] = env_init[e];
+  {
+    int32_t* cnt = (int32_t*)(img.data() + mp.off_cnt);
+    cnt[0] = (int32_t)next_sample;
+    cnt[1] = (next_sample > 0 && p->basis_schedule == HM_ZX_ALTERNATE && ((next_sample - 1) & 1)) ? 1 : 0;
+  }
   cudaError_t e = cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
@@ -745,6 +753,19 @@ int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_ch
   ctx->chains[id] = ch;
   *out = id;
   return HM_OK;
+}
+
+int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_chain* out) {
+  return init_chain_impl(ctx, p, env_init, 0, out);
+}
+
+int hm_resume_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_out, int64_t next_sample,
+                    hm_chain* out) {
+  if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
+  if (next_sample < 1 || next_sample > INT32_MAX)
+    return fail(&ctx->err, HM_ERR_ARG, "next_sample must be in [1, 2^31 - 1] (hm_init_chain starts at 0)");
+  if (!env_out) return fail(&ctx->err, HM_ERR_ARG, "a resumed chain needs its environment outcomes");
+  return init_chain_impl(ctx, p, env_out, next_sample, out);
 }
 
 int hm_free_chain(hm_ctx* ctx, hm_chain chain) {

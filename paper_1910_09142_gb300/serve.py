@@ -46,6 +46,7 @@ class Job:
         self.bytes = 0
         self.bin_size = int(bin_size)
         self.estimator = None                # Estimator over the kept samples
+        self.resume_from = None              # (outcomes, sample index) of a checkpoint
 
     def estimate(self):
         """Mean of every observable over the kept samples, and its binned
@@ -58,6 +59,16 @@ class Job:
     @property
     def complete(self):
         return self.done_steps >= self.n_warmup + self.n_samples
+
+    def checkpoint(self):
+        """Everything needed to continue this job elsewhere, as plain data:
+        its parameters, the outcomes of its last collapse, its sample index
+        and the samples kept so far.  Step 4 resets the cluster to Bell
+        pairs, so no MPS is saved."""
+        return dict(params={f: getattr(self.params, f) for f, _ in binding.Params._fields_},
+                    env=[int(x) for x in self.env[-1]] if self.env else None,
+                    next_sample=self.done_steps, n_samples=self.n_samples, n_warmup=self.n_warmup,
+                    bin_size=self.bin_size, results=[[float(x) for x in r] for r in self.results])
 
 
 class Server:
@@ -94,13 +105,32 @@ class Server:
         self.queue.append(job)
         return job
 
+    def resume(self, ckpt):
+        """Queue a job from ``Job.checkpoint()`` data; it continues with the
+        draws the interrupted job would have made (hm_resume_chain)."""
+        job = self.submit(binding.Params(**ckpt["params"]), ckpt["n_samples"], ckpt["n_warmup"])
+        job.bin_size = int(ckpt["bin_size"])
+        job.done_steps = int(ckpt["next_sample"])
+        for r in ckpt["results"]:
+            job.results.append(np.array(r))
+            if job.estimator is None:
+                job.estimator = Estimator(len(r), job.bin_size)
+            job.estimator.add(job.id, r)
+        if job.done_steps > 0:
+            job.resume_from = (np.array(ckpt["env"], dtype=np.int8), job.done_steps)
+        return job
+
     def _admit(self):
         while self.queue and len(self.active) < self.max_chains:
             job = self.queue[0]
             if self.used + job.bytes > self.capacity:
                 break                                  # FIFO: later jobs wait behind it
             self.queue.popleft()
-            job.chain = self.ctx.init_chain(job.params)
+            if job.resume_from is not None:
+                env, n = job.resume_from
+                job.chain = self.ctx.init_chain(job.params, env_init=env, next_sample=n)
+            else:
+                job.chain = self.ctx.init_chain(job.params)
             job.admitted = self.clock()
             self.used += job.bytes
             self.active.append(job)

@@ -160,3 +160,10 @@ def test_invalid_parameters_rejected(lib, kw):
     with pytest.raises(binding.HmError) as e:
         binding.num_obs(binding.params(**kw))
     assert e.value.code == binding.HM_ERR_ARG
+
+
+def test_resume_without_context_is_an_argument_error(lib):
+    import ctypes
+    out = ctypes.c_int64()
+    p = binding.params(3, 2)
+    assert lib.hm_resume_chain(None, ctypes.byref(p), None, 2, ctypes.byref(out)) == binding.HM_ERR_ARG

@@ -62,3 +62,23 @@ def test_binned_error():
     with pytest.raises(ValueError):
         chain.binned_error([1.0], 2)
     assert model is not None
+
+
+@pytest.mark.parametrize("basis_zx,cut", [(True, 2), (True, 3), (False, 2)])
+def test_resume_from_checkpoint_is_exact(basis_zx, cut):
+    """Between samples a chain is only its environment outcomes and the sample
+    index: step 4 resets the cluster to Bell pairs.  A chain rebuilt from the
+    outcomes of sample cut-1 (read in that sample's basis) and index cut
+    draws exactly what the uninterrupted chain draws."""
+    cfg = dict(Lx=3, two_W=2, J_leg=1.0, J_rung=0.7, beta=0.6, tau=0.1, chi_max=16, cutoff=1e-10,
+               seed=9, chain_id=2, basis_zx=basis_zx)
+    full = chain.HybridChain(**cfg)
+    recs = [full.sample() for _ in range(cut + 2)]
+    res = chain.HybridChain(**cfg)
+    res.env = list(recs[cut - 1]["env_out"])
+    res.env_basis = collapse.sample_basis(cut - 1, basis_zx)     # derived from the index alone
+    assert res.env_basis == recs[cut - 1]["basis"]
+    res.n = cut
+    for r in recs[cut:]:
+        q = res.sample()
+        assert np.array_equal(q["obs"], r["obs"]) and q["env_out"] == r["env_out"] and q["logp"] == r["logp"]

@@ -23,10 +23,10 @@ class FakeCtx:
     def __init__(self):
         self.chains, self.next, self.calls = {}, 1, []
 
-    def init_chain(self, p):
+    def init_chain(self, p, env_init=None, next_sample=0):
         cid = self.next
         self.next += 1
-        self.chains[cid] = [p, 0]
+        self.chains[cid] = [p, next_sample]
         return cid
 
     def evolve(self, ids):
@@ -213,3 +213,27 @@ def test_poisson_stream_served_end_to_end():
     assert st["latency_p50_s"] == pytest.approx(1.0)
     for job in srv.finished:
         assert len(job.results) == job.n_samples and job.admitted >= job.arrival
+
+
+def test_checkpoint_and_resume_continue_the_job_exactly():
+    import json
+    whole = serve.Server(FakeCtx(), 1 << 40)
+    ref = whole.submit(_p(4, 5), 7, 2)
+    whole.run()
+    first = serve.Server(FakeCtx(), 1 << 40)
+    job = first.submit(_p(4, 5), 7, 2)
+    job.bin_size = 3
+    for _ in range(4):
+        first.step()
+    ckpt = json.loads(json.dumps(job.checkpoint()))        # plain data, survives a round trip
+    assert ckpt["next_sample"] == 4 and len(ckpt["results"]) == 2 and len(ckpt["env"]) == ckpt_env_len(job)
+    second = serve.Server(FakeCtx(), 1 << 40)
+    again = second.resume(ckpt)
+    second.run()
+    assert again.complete and len(again.results) == 7
+    assert all(np.array_equal(x, y) for x, y in zip(again.results, ref.results))
+    assert np.allclose(again.estimate()[0], np.array(ref.results).mean(axis=0), atol=1e-12)
+
+
+def ckpt_env_len(job):
+    return binding.num_env(job.params)
