@@ -135,6 +135,25 @@ class Server:
             self.used += job.bytes
             self.active.append(job)
 
+    def checkpoint(self):
+        """Checkpoint of every job, finished, resident or queued, as plain
+        data (see ``Job.checkpoint``).  Taken between ticks, no kernel of
+        this server is in flight; a restarted server continues from it."""
+        jobs = self.finished + self.active + list(self.queue)
+        return {"jobs": [j.checkpoint() for j in sorted(jobs, key=lambda j: j.id)]}
+
+    @classmethod
+    def restore(cls, ckpt, ctx, arena_bytes, **kw):
+        """A new server holding the jobs of ``checkpoint()``: finished ones
+        keep their results, the others are queued to resume."""
+        srv = cls(ctx, arena_bytes, **kw)
+        for jc in ckpt["jobs"]:
+            job = srv.resume(jc)
+            if job.complete:
+                srv.queue.remove(job)
+                srv.finished.append(job)
+        return srv
+
     # -- one tick -----------------------------------------------------------------------
     def step(self):
         """Admit what fits, then one Markov step of every resident chain.

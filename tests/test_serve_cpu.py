@@ -237,3 +237,53 @@ def test_checkpoint_and_resume_continue_the_job_exactly():
 
 def ckpt_env_len(job):
     return binding.num_env(job.params)
+
+
+def _crashing_worker(path, crash_after, out):
+    """A serving worker that checkpoints after every tick and dies (exit 3,
+    no cleanup) after ``crash_after`` ticks, or resumes from ``path``."""
+    import json
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_1910_09142_gb300 import serve as srv_mod
+    if os.path.exists(path):
+        with open(path) as f:
+            srv = srv_mod.Server.restore(json.load(f), FakeCtx(), 1 << 40)
+    else:
+        srv = srv_mod.Server(FakeCtx(), 1 << 40)
+        for i, (lx, n, w) in enumerate([(3, 5, 1), (4, 3, 0), (5, 6, 2)]):
+            srv.submit(_p(lx, i), n, w)
+    ticks = 0
+    while srv.step():
+        ticks += 1
+        with open(path + ".tmp", "w") as f:
+            json.dump(srv.checkpoint(), f)
+        os.replace(path + ".tmp", path)
+        if crash_after and ticks == crash_after:
+            os._exit(3)
+    out["results"] = {j.id: [list(r) for r in j.results] for j in srv.finished}
+
+
+def test_serving_worker_crash_restarts_from_checkpoint(tmp_path):
+    """A failure made on the host, with no GPU involved: the worker process
+    exits mid-run, and a new one restores the last checkpoint and finishes
+    with the results of an uninterrupted run."""
+    import multiprocessing as mpl
+    ctx = mpl.get_context("spawn")
+    path = str(tmp_path / "serve.json")
+    out = ctx.Manager().dict()
+    p = ctx.Process(target=_crashing_worker, args=(path, 3, out))
+    p.start()
+    p.join(60)
+    assert p.exitcode == 3 and "results" not in out
+    p = ctx.Process(target=_crashing_worker, args=(path, 0, out))
+    p.start()
+    p.join(60)
+    assert p.exitcode == 0
+    whole = serve.Server(FakeCtx(), 1 << 40)
+    jobs = [whole.submit(_p(lx, i), n, w) for i, (lx, n, w) in enumerate([(3, 5, 1), (4, 3, 0), (5, 6, 2)])]
+    whole.run()
+    got = out["results"]
+    for j in jobs:
+        assert np.array_equal(np.array(got[j.id]), np.array(j.results)), j.id
