@@ -43,7 +43,7 @@ def build(verbose=False, extra=()):
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         logs = list(ex.map(compile_one, range(len(SOURCES))))
-    cmd = [cc, *ARCH, "-shared", "--cudart", "static", "-o", LIB, *objs]
+    cmd = [cc, *ARCH, "-shared", "--cudart", "static", "-o", LIB, *objs, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

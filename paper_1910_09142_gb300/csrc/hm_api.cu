@@ -2,6 +2,7 @@
 // ladder site map and Trotter/swap schedule planner, the gate table, the
 // arena allocator and the entry points.  All device work is in hm_fp64.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -527,6 +528,14 @@ struct Scratch {   // temporary arena block for host-output calls
 
 void hm::set_global_error(const char* msg) { g_err = msg; }
 
+namespace {
+// Named NVTX range over one entry point (a no-op unless a profiler attaches).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
+
 extern "C" {
 
 int hm_create(hm_ctx** out, int device, void* dev_mem, size_t bytes, void* cuda_stream) {
@@ -781,6 +790,7 @@ int hm_free_chain(hm_ctx* ctx, hm_chain chain) {
 }
 
 int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
+  Range range("hm_evolve");
   std::vector<Chain*> cs;
   int rc = lookup(ctx, ids, n, &cs);
   if (rc) return rc;
@@ -836,6 +846,7 @@ static int measure_impl(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out
 }
 
 int hm_measure_cluster_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out_dev, int32_t n_obs) {
+  Range range("hm_measure_cluster_device");
   if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
   if (!out_dev && n > 0) return fail(&ctx->err, HM_ERR_ARG, "null output");
   std::vector<Chain*> cs;
@@ -843,6 +854,7 @@ int hm_measure_cluster_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, doubl
 }
 
 int hm_measure_cluster(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out, int32_t n_obs) {
+  Range range("hm_measure_cluster");
   if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
   if (!out && n > 0) return fail(&ctx->err, HM_ERR_ARG, "null output");
   if (n == 0) return HM_OK;
@@ -857,6 +869,7 @@ int hm_measure_cluster(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out,
 }
 
 int hm_measure_susceptibility(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out) {
+  Range range("hm_measure_susceptibility");
   if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
   if (n == 0) return HM_OK;
   if (!out) return fail(&ctx->err, HM_ERR_ARG, "null output");
@@ -915,12 +928,14 @@ static int collapse_impl(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* en
 }
 
 int hm_collapse_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out_dev, double* logp_out_dev) {
+  Range range("hm_collapse_device");
   if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
   std::vector<Chain*> cs;
   return collapse_impl(ctx, ids, n, env_out_dev, logp_out_dev, cs);
 }
 
 int hm_collapse(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, double* logp_out) {
+  Range range("hm_collapse");
   if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
   if (n == 0) return HM_OK;
   if (!env_out && !logp_out) {
