@@ -216,9 +216,12 @@ int hm_set_mps(hm_ctx* ctx, hm_chain chain, const int32_t* dims, int32_t n_sites
 /* Run an explicit list of n_ops two-site ops on one chain (debugging and
  * kernel-level parity).  ops[4 i ..]: (site k, gate, absorb, exact) with gate
  * index into the chain's gate table (0 = identity, 1 = SWAP, 2 + b = bond b
- * of the sorted bond list at tau/2), absorb 0 = left (A_k <- U S), 1 = right
- * (A_{k+1} <- S V^T), exact 1 = keep every nonzero singular value up to the
- * old bond dim without renormalising (a centre move).  Asynchronous. */
+ * of the sorted bond list at tau/2, then a fused chain's product gates; see
+ * hm_gates), absorb 0 = left (A_k <- U S), 1 = right (A_{k+1} <- S V^T),
+ * exact 1 = keep every nonzero singular value up to the old bond dim without
+ * renormalising (a centre move).  The op list is staged in the arena, so the
+ * call synchronises the stream; HM_ERR_ARG for an op outside the chain or
+ * the table. */
 int hm_apply_ops(hm_ctx* ctx, hm_chain chain, const int32_t* ops, int32_t n_ops);
 
 /* The op schedule of hm_evolve (host planner; no GPU needed): writes up to

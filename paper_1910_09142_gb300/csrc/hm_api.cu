@@ -439,6 +439,7 @@ struct Chain {
   Layout L;
   MemPlan mp;
   std::vector<OpDev> ops;
+  int32_t n_gates = 0;              // gate table entries on the device
   size_t off = 0;
   ChainDev* dev = nullptr;          // device address of the descriptor
   int phase = 0;                    // 0 initial state, 1 evolved
@@ -643,6 +644,7 @@ static int init_chain_impl(hm_ctx* ctx, const hm_params* p, const int8_t* env_in
   ch->L = make_layout(*p);
   Schedule sched = make_schedule(ch->L);
   ch->ops = std::move(sched.ops);
+  ch->n_gates = sched.n_gates();
   ch->mp = mem_plan(*p, ch->L, ch->ops.size(), sched.gates.size() / 81);
   ch->n_obs = 1 + 2 * (int)ch->L.meas.size();
   {
@@ -1035,7 +1037,7 @@ int hm_apply_ops(hm_ctx* ctx, hm_chain chain, const int32_t* ops, int32_t n_ops)
   Chain* c = it->second;
   if (n_ops <= 0) return HM_OK;
   if (!ops) return fail(&ctx->err, HM_ERR_ARG, "null op list");
-  const int ng = (int)(GATE_BOND0 + c->L.bonds.size());
+  const int ng = c->n_gates;
   std::vector<OpDev> v(n_ops);
   for (int i = 0; i < n_ops; ++i) {
     v[i] = {ops[4 * i], ops[4 * i + 1], ops[4 * i + 2], ops[4 * i + 3]};
