@@ -137,7 +137,9 @@ int hm_num_env(const hm_params* p, int32_t* n_env);
 
 /* Allocate a chain and write its first initial state (step 1).  env_init:
  * host array of n_env outcomes in {0,1,2} (Sz basis: m = +1, 0, -1), or NULL
- * to draw them from the chain's Philox stream with sample index n = -1. */
+ * to draw them from the chain's Philox stream with sample index n = -1.
+ * Synchronises the stream (the chain image is uploaded from the host).
+ * HM_ERR_NOMEM, with nothing allocated, when the arena cannot hold it. */
 int hm_init_chain(hm_ctx* ctx, const hm_params* p, const int8_t* env_init, hm_chain* out);
 
 /* Resume a chain from its checkpoint (no counterpart in the paper; the
