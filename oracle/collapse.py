@@ -21,8 +21,9 @@ Readings where the paper is silent:
   u < cumulative p_b (else the last b with p_b > 0).  The initial environment
   is drawn in the S^z basis with p = 1/3 each and n = -1.
 
-Pins: ``tests/test_oracle_collapse.py`` (Philox known-answer vectors, brute
-force enumeration of collapse probabilities, detailed balance).
+Pins: ``tests/test_oracle_collapse.py`` (Philox against cuRAND's host
+generator of the same kind, brute force enumeration of collapse
+probabilities, detailed balance).
 """
 import math
 

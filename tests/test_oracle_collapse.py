@@ -1,31 +1,76 @@
 """Pins of oracle/collapse.py and oracle/brute.py.
 
-* Philox4x32-10 against the published known-answer vectors of Salmon et al.
-  (SC'11; the Random123 distribution's kat_vectors for philox4x32, 10 rounds);
+* Philox4x32-10 against a library implementation of the same generator:
+  cuRAND's host-side CURAND_RNG_PSEUDO_PHILOX4_32_10, whose output stream for
+  seed s is the blocks philox4x32_10((0, 0, j, 0), (s mod 2^32, s >> 32)),
+  j = 0, 1, ...  This covers the round function, multipliers, key schedule
+  and round count for keys with every bit pattern tried.  Counter words 0, 1
+  and 3, which that stream leaves at zero, must each change the output;
 * collapse: the product of the sequential conditional probabilities equals the
   brute-force joint probability ||Pi_j psi||^2 of every outcome (Sec. I.C.2);
 * detailed balance P_i p(i->j) = P_j p(j->i) and stationarity across a change
   of measurement basis, by brute force on a tiny ladder (Sec. I.C.2).
 """
+import ctypes
+import ctypes.util
+import glob
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
 
 from oracle import brute, collapse, ed, model, mps
 
-KAT = [  # (counter, key, output), Philox4x32-10
-    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
-    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
-    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
-     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
-]
+CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161      # curandRngType_t of cuRAND's public header
 
 
-@pytest.mark.parametrize("ctr,key,out", KAT)
-def test_philox_known_answers(ctr, key, out):
-    assert collapse.philox4x32_10(ctr, key) == out
+def _curand():
+    """cuRAND from the CUDA toolkit (host generator only; no GPU needed)."""
+    paths = sorted(glob.glob(os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib*", "libcurand.so*")))
+    name = ctypes.util.find_library("curand")
+    for path in paths + ([name] if name else []):
+        try:
+            return ctypes.CDLL(path)
+        except OSError:
+            continue
+    pytest.skip("cuRAND not found")
+
+
+def _curand_stream(lib, seed, n_blocks):
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        buf = (ctypes.c_uint32 * (4 * n_blocks))()
+        assert lib.curandGenerate(gen, buf, ctypes.c_size_t(4 * n_blocks)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return [tuple(buf[4 * j:4 * j + 4]) for j in range(n_blocks)]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0x0123456789ABCDEF, 0xFEDCBA9876543210, 0xFFFFFFFFFFFFFFFF])
+def test_philox_matches_the_curand_host_generator(seed):
+    lib = _curand()
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for j, block in enumerate(_curand_stream(lib, seed, 300)):
+        assert collapse.philox4x32_10((0, 0, j, 0), key) == block, j
+
+
+def test_philox_uses_every_counter_word():
+    key = (0x9E3779B9, 0x7F4A7C15)
+    outs = {}
+    for c in itertools.product((0, 1, 0xFFFFFFFF), repeat=4):
+        outs[c] = collapse.philox4x32_10(c, key)
+    assert len(set(outs.values())) == len(outs)               # a bijection of the counter
+    base = outs[(0, 0, 0, 0)]
+    for w in range(4):
+        c = [0, 0, 0, 0]
+        c[w] = 1
+        x = np.array(outs[tuple(c)], dtype=np.uint64) ^ np.array(base, dtype=np.uint64)
+        # one flipped input bit changes about half of the 128 output bits
+        assert 40 < sum(bin(int(v)).count("1") for v in x) < 88, w
 
 
 def test_uniform_range_and_moments():
