@@ -15,7 +15,8 @@ Readings where the paper is silent: the kept count is additionally capped at
 chi_max, and is lowered to the nearest gap so that a (near-)degenerate
 multiplet, s_{k+1} >= s_k (1 - 1e-8), is never split.
 
-Library primitives used as steps: numpy SVD (LAPACK gesdd) and QR (geqrf).
+Library primitives used as steps: numpy SVD (LAPACK gesdd, with gesvd when
+gesdd does not converge) and QR (geqrf).
 Pins: ``tests/test_oracle_mps.py`` (dense Trotter evolver, single-rung closed
 form, pure-ancilla limit against exact diagonalisation).
 """
@@ -75,6 +76,18 @@ def truncation_rank(s, chi_max, cutoff):
     return k
 
 
+def thin_svd(m):
+    """Thin SVD, a library step: LAPACK gesdd, or gesvd when gesdd does not
+    converge.  That happens on strongly rank-deficient two-site tensors, for
+    example a fully polarised environment around a small cluster.  Both
+    drivers compute the same decomposition."""
+    try:
+        return np.linalg.svd(m, full_matrices=False)
+    except np.linalg.LinAlgError:
+        import scipy.linalg
+        return scipy.linalg.svd(m, full_matrices=False, lapack_driver="gesvd")
+
+
 def split(mps, k, gate, absorb, chi_max, cutoff):
     """Apply a 9x9 gate to sites (k, k+1) and split by a truncated SVD.
 
@@ -89,7 +102,7 @@ def split(mps, k, gate, absorb, chi_max, cutoff):
     theta = np.tensordot(a, b, axes=(2, 0))                     # (l, s1, s2, r)
     g = np.asarray(gate).reshape(D, D, D, D)                     # (a, b, s1, s2)
     theta = np.einsum("abst,lstr->labr", g, theta)
-    u, s, vt = np.linalg.svd(theta.reshape(chil * D, D * chir), full_matrices=False)
+    u, s, vt = thin_svd(theta.reshape(chil * D, D * chir))
     kk = truncation_rank(s, chi_max, cutoff)
     w = s * s
     discarded = float(np.sum(w[kk:]) / np.sum(w))

@@ -147,7 +147,7 @@ def split(st, k, gate, absorb, chi_max, cutoff, sizes=None):
         raise FloatingPointError("two-site tensor breaks S^z conservation")
     parts = []
     for q, rows, cols in _blocks(row_q, col_q):
-        u, s, vt = np.linalg.svd(theta[np.ix_(rows, cols)], full_matrices=False)
+        u, s, vt = mpsmod.thin_svd(theta[np.ix_(rows, cols)])
         parts.append((q, rows, cols, u, s, vt))
         if sizes is not None:
             sizes.append((len(rows), len(cols)))
