@@ -440,6 +440,7 @@ struct Chain {
   MemPlan mp;
   std::vector<OpDev> ops;
   int32_t n_gates = 0;              // gate table entries on the device
+  double cost = 0.0;                // dense-SVD flops of all ops at the bond caps
   size_t off = 0;
   ChainDev* dev = nullptr;          // device address of the descriptor
   int phase = 0;                    // 0 initial state, 1 evolved
@@ -646,6 +647,11 @@ static int init_chain_impl(hm_ctx* ctx, const hm_params* p, const int8_t* env_in
   ch->ops = std::move(sched.ops);
   ch->n_gates = sched.n_gates();
   ch->mp = mem_plan(*p, ch->L, ch->ops.size(), sched.gates.size() / 81);
+  for (const OpDev& op : ch->ops) {
+    const double m = 3.0 * ch->mp.bmax[op.k], q = 3.0 * ch->mp.bmax[op.k + 2];
+    const double M = std::max(m, q), N = std::min(m, q);
+    ch->cost += 4.0 * M * M * N + 8.0 * M * N * N + 9.0 * N * N * N;
+  }
   ch->n_obs = 1 + 2 * (int)ch->L.meas.size();
   {
     // at most 8 measured bonds may start on one site (measure kernel buffer)
@@ -810,6 +816,11 @@ int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
         max_ops = std::max<int>(max_ops, (int)c->ops.size());
         chi_cap = std::max<int>(chi_cap, c->mp.chi_cap);
       }
+    // Costliest chains first: CTAs start roughly in index order, so an
+    // uneven batch ends closer to its average load (longest processing time
+    // first), and each launch of <= kMaxBatch chains holds similar costs.
+    // Equal costs keep the caller's order.
+    std::stable_sort(group.begin(), group.end(), [](const Chain* a, const Chain* b) { return a->cost > b->cost; });
     rc = for_batches(group, [&](BatchArg& b, int) {
       const int chunk = 4096;
       for (int t0 = 0; t0 < max_ops; t0 += chunk) {
