@@ -122,6 +122,19 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
+def _device_buffer(t, dtype, numel, device, name):
+    """Device pointer of a caller tensor the kernels write ``numel`` elements
+    into; refuses anything they could write past or misread."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != device:
+        raise ValueError("%s must be a CUDA tensor on cuda:%d" % (name, device))
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor" % (name, dtype))
+    if t.numel() < numel:
+        raise ValueError("%s holds %d elements, %d needed" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _ids(ids):
     arr = np.ascontiguousarray(np.asarray(ids, dtype=np.int64))
     return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
@@ -200,6 +213,7 @@ class Context:
         _check(self.lib.hm_create(ctypes.byref(h), device, ctypes.c_void_p(self._arena.data_ptr()),
                                   int(arena_bytes), ctypes.c_void_p(s.cuda_stream)))
         self.h = h
+        self._n_env = {}                 # chain -> environment sites (collapse output width)
 
     def close(self):
         if getattr(self, "h", None):
@@ -226,10 +240,12 @@ class Context:
                                              ctypes.byref(out)))
         else:
             self._c(self.lib.hm_init_chain(self.h, ctypes.byref(p), _ptr(env), ctypes.byref(out)))
+        self._n_env[out.value] = num_env(p)
         return out.value
 
     def free_chain(self, cid):
         self._c(self.lib.hm_free_chain(self.h, cid))
+        self._n_env.pop(cid, None)
 
     def evolve(self, ids):
         arr, ptr = _ids(ids)
@@ -242,9 +258,12 @@ class Context:
         return out
 
     def measure_device(self, ids, out_tensor):
+        """Observables into a (len(ids), n_obs) float64 CUDA tensor, asynchronously."""
+        import torch
         arr, ptr = _ids(ids)
-        self._c(self.lib.hm_measure_cluster_device(self.h, ptr, len(arr), ctypes.c_void_p(out_tensor.data_ptr()),
-                                                   out_tensor.shape[-1]))
+        n_obs = out_tensor.shape[-1]
+        buf = _device_buffer(out_tensor, torch.float64, len(arr) * n_obs, self.device, "out_tensor")
+        self._c(self.lib.hm_measure_cluster_device(self.h, ptr, len(arr), buf, n_obs))
 
     def susceptibility(self, ids):
         """(chi_M, double sum) per chain, Eq. sus."""
@@ -261,9 +280,21 @@ class Context:
         return env[:, :n_env], logp
 
     def collapse_device(self, ids, env_tensor=None, logp_tensor=None):
+        """Collapse and reset, asynchronously; outcomes into an int8 CUDA tensor
+        of (len(ids), n_env) and log-probabilities into a float64 one of
+        len(ids), either may be None.  Every chain must have the same n_env
+        when env_tensor is given."""
+        import torch
         arr, ptr = _ids(ids)
-        e = ctypes.c_void_p(env_tensor.data_ptr()) if env_tensor is not None else None
-        lp = ctypes.c_void_p(logp_tensor.data_ptr()) if logp_tensor is not None else None
+        e = lp = None
+        if env_tensor is not None:
+            widths = {self._n_env.get(int(c), 0) for c in arr}
+            if len(widths) > 1:
+                raise ValueError("chains of one collapse call must share n_env when env_tensor is given")
+            n_env = widths.pop() if widths else 0
+            e = _device_buffer(env_tensor, torch.int8, len(arr) * n_env, self.device, "env_tensor")
+        if logp_tensor is not None:
+            lp = _device_buffer(logp_tensor, torch.float64, len(arr), self.device, "logp_tensor")
         self._c(self.lib.hm_collapse_device(self.h, ptr, len(arr), e, lp))
 
     def stats(self, cid):

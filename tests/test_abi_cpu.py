@@ -167,3 +167,10 @@ def test_resume_without_context_is_an_argument_error(lib):
     out = ctypes.c_int64()
     p = binding.params(3, 2)
     assert lib.hm_resume_chain(None, ctypes.byref(p), None, 2, ctypes.byref(out)) == binding.HM_ERR_ARG
+
+
+def test_device_output_buffers_are_checked_before_any_launch():
+    import torch
+    for t in (torch.zeros(6, dtype=torch.float64), np.zeros(6)):        # host memory
+        with pytest.raises(ValueError):
+            binding._device_buffer(t, torch.float64, 6, 0, "out")
