@@ -65,9 +65,14 @@ class Job:
         its parameters, the outcomes of its last collapse, its sample index
         and the samples kept so far.  Step 4 resets the cluster to Bell
         pairs, so no MPS is saved."""
-        return dict(params={f: getattr(self.params, f) for f, _ in binding.Params._fields_},
-                    env=[int(x) for x in self.env[-1]] if self.env else None,
-                    next_sample=self.done_steps, n_samples=self.n_samples, n_warmup=self.n_warmup,
+        if self.env:
+            env = [int(x) for x in self.env[-1]]
+        elif self.resume_from is not None:            # resumed, no step since
+            env = [int(x) for x in self.resume_from[0]]
+        else:
+            env = None
+        return dict(id=self.id, params={f: getattr(self.params, f) for f, _ in binding.Params._fields_},
+                    env=env, next_sample=self.done_steps, n_samples=self.n_samples, n_warmup=self.n_warmup,
                     bin_size=self.bin_size, results=[[float(x) for x in r] for r in self.results])
 
 
@@ -94,21 +99,24 @@ class Server:
         self._next_id = 0
 
     # -- requests ---------------------------------------------------------------------
-    def submit(self, params, n_samples, n_warmup=0, arrival=None):
+    def submit(self, params, n_samples, n_warmup=0, arrival=None, job_id=None):
         """Queue a job; returns it.  ``params`` is a binding.Params; ``arrival``
-        (clock time the request came in) defaults to now."""
-        job = Job(self._next_id, params, n_samples, n_warmup, self.clock() if arrival is None else arrival)
+        (clock time the request came in) defaults to now; ``job_id`` keeps a
+        restored job's identity (default: the next free id)."""
+        jid = self._next_id if job_id is None else int(job_id)
+        job = Job(jid, params, n_samples, n_warmup, self.clock() if arrival is None else arrival)
         job.bytes = self.query_memory(params)
         if job.bytes > self.capacity:
             raise ValueError("job %d needs %d bytes, more than the whole arena" % (job.id, job.bytes))
-        self._next_id += 1
+        self._next_id = max(self._next_id, jid + 1)
         self.queue.append(job)
         return job
 
     def resume(self, ckpt):
         """Queue a job from ``Job.checkpoint()`` data; it continues with the
         draws the interrupted job would have made (hm_resume_chain)."""
-        job = self.submit(binding.Params(**ckpt["params"]), ckpt["n_samples"], ckpt["n_warmup"])
+        job = self.submit(binding.Params(**ckpt["params"]), ckpt["n_samples"], ckpt["n_warmup"],
+                          job_id=ckpt.get("id"))
         job.bin_size = int(ckpt["bin_size"])
         job.done_steps = int(ckpt["next_sample"])
         for r in ckpt["results"]:

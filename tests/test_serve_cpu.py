@@ -287,3 +287,22 @@ def test_serving_worker_crash_restarts_from_checkpoint(tmp_path):
     got = out["results"]
     for j in jobs:
         assert np.array_equal(np.array(got[j.id]), np.array(j.results)), j.id
+
+
+def test_checkpoint_of_a_resumed_job_before_its_next_step():
+    srv = serve.Server(FakeCtx(), 1 << 40)
+    job = srv.submit(_p(3, 7), 5, 0)
+    srv.step()
+    srv.step()
+    ckpt = job.checkpoint()
+    other = serve.Server(FakeCtx(), 1 << 40)
+    other._next_id = 10
+    again = other.resume(ckpt)
+    assert again.id == job.id and other._next_id == 10
+    ckpt2 = again.checkpoint()                          # no step since the resume
+    assert ckpt2["env"] == ckpt["env"] and ckpt2["next_sample"] == 2
+    third = serve.Server(FakeCtx(), 1 << 40)
+    last = third.resume(ckpt2)
+    third.run()
+    srv.run()
+    assert all(np.array_equal(x, y) for x, y in zip(last.results, job.results)) and len(last.results) == 5
