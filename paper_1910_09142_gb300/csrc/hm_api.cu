@@ -809,11 +809,10 @@ int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
   o.ctx_err = ctx->err_word;
   for (int prec : {HM_FP64, HM_MIXED}) {
     std::vector<Chain*> group;
-    int max_ops = 0, chi_cap = 1;
+    int chi_cap = 1;
     for (Chain* c : cs)
       if (c->p.precision == prec) {
         group.push_back(c);
-        max_ops = std::max<int>(max_ops, (int)c->ops.size());
         chi_cap = std::max<int>(chi_cap, c->mp.chi_cap);
       }
     // Costliest chains first: CTAs start roughly in index order, so an
@@ -821,9 +820,11 @@ int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
     // first), and each launch of <= kMaxBatch chains holds similar costs.
     // Equal costs keep the caller's order.
     std::stable_sort(group.begin(), group.end(), [](const Chain* a, const Chain* b) { return a->cost > b->cost; });
-    rc = for_batches(group, [&](BatchArg& b, int) {
+    rc = for_batches(group, [&](BatchArg& b, int s) {
       const int chunk = 4096;
-      for (int t0 = 0; t0 < max_ops; t0 += chunk) {
+      int batch_ops = 0;                          // this launch's longest op list
+      for (int i = 0; i < b.n; ++i) batch_ops = std::max<int>(batch_ops, (int)group[s + i]->ops.size());
+      for (int t0 = 0; t0 < batch_ops; t0 += chunk) {
         b.t0 = t0;
         b.t1 = t0 + chunk;
         const int r = prec == HM_FP64 ? launch_evolve_fp64(b, o, ctx->stream)
