@@ -32,7 +32,8 @@ def host(tmp_path_factory):
     src = [os.path.join(ROOT, "paper_1910_09142_gb300", "csrc", "hm_api.cu"),
            os.path.join(ROOT, "tests", "host_abi", "cuda_stub.cpp")]
     r = subprocess.run([cxx, "-std=c++17", "-O1", "-shared", "-fPIC", "-x", "c++", src[0], "-x", "c++", src[1],
-                        "-I" + inc, "-o", out, "-ldl"], capture_output=True, text=True)
+                        "-I" + inc, "-o", out, "-ldl", "-Wl,-Bsymbolic"],   # the stub, not a loaded cudart
+                       capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     lib = ctypes.CDLL(out)
     P, vp, i32, i64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
