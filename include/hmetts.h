@@ -21,7 +21,13 @@
  * - Memory: the caller hands one device buffer to hm_create(); the library
  *   sub-allocates every chain and workspace inside it and never calls
  *   cudaMalloc itself.  Host pointers passed in are owned by the caller and
- *   only need to stay valid until the call returns.
+ *   only need to stay valid until the call returns.  Calls with HOST outputs
+ *   (hm_measure_cluster, hm_collapse with an output pointer,
+ *   hm_measure_susceptibility) and hm_apply_ops stage through a temporary
+ *   arena block of their output size (n * n_obs doubles; n * n_env bytes
+ *   plus n doubles; n doubles; the op list), released before they return.
+ *   They fail with HM_ERR_NOMEM when the arena has no such block free; the
+ *   _device variants need none.
  * - Streams: all device work of a context is issued on the CUDA stream given
  *   to hm_create() (NULL = legacy default stream).  Calls that return host
  *   data synchronise that stream before returning; the others are

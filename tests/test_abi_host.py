@@ -241,3 +241,23 @@ def test_apply_ops_accepts_the_fused_product_gates_only_inside_the_table(host):
         ops = np.array([[0, gate, 1, 0]], dtype=np.int32)
         assert host.hm_apply_ops(ctx.h, cid, ops.ctypes.data_as(ctypes.c_void_p), 1) == want
     ctx.close()
+
+
+def test_host_outputs_need_a_staging_block_device_outputs_do_not(host):
+    p = binding.params(3, 2, beta=0.4, tau=0.1, chi_max=16)
+    need = binding.query_memory(p)
+    n_obs = binding.num_obs(p)
+    ctx = Ctx(host, need + 256)                          # the chain plus the error word, nothing more
+    host.hm_measure_cluster_device.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                               ctypes.c_void_p, ctypes.c_int32]
+    rc, cid = ctx.init(p)
+    assert rc == 0
+    a, ptr = ctx.ids([cid])
+    assert host.hm_evolve(ctx.h, ptr, 1) == 0
+    out = np.zeros(n_obs)
+    assert host.hm_measure_cluster(ctx.h, ptr, 1, out.ctypes.data_as(ctypes.c_void_p), n_obs) \
+        == binding.HM_ERR_NOMEM
+    dev = np.zeros(n_obs)                                # stands in for a caller's device buffer
+    assert host.hm_measure_cluster_device(ctx.h, ptr, 1, dev.ctypes.data_as(ctypes.c_void_p), n_obs) == 0
+    assert host.hm_collapse(ctx.h, ptr, 1, None, None) == 0
+    ctx.close()
