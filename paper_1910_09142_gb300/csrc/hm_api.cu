@@ -999,6 +999,10 @@ int hm_get_mps(hm_ctx* ctx, hm_chain chain, int32_t* dims_out, int32_t dims_cap,
   HM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   char* base = ctx->base + c->off;
   HM_CUDA(ctx, cudaMemcpy(dims_out, base + c->mp.off_chi, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  for (int i = 0; i <= n; ++i)   // never size a copy from a bond dim outside its slot
+    if (dims_out[i] < 1 || dims_out[i] > c->mp.bmax[i])
+      return fail(&ctx->err, HM_ERR_NUMERIC, "bond %d holds dim %d outside [1, %lld]", i, dims_out[i],
+                  (long long)c->mp.bmax[i]);
   size_t tot = 0;
   for (int s = 0; s < n; ++s) tot += (size_t)dims_out[s] * 3 * dims_out[s + 1];
   if (n_doubles_out) *n_doubles_out = tot;

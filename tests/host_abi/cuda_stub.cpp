@@ -82,4 +82,5 @@ int hmtest_chain_ints(const void* p, int32_t* out8) {
 const void* hmtest_chain_ops(const void* p) { return ((const hm::ChainDev*)p)->ops; }
 const double* hmtest_chain_gates(const void* p) { return ((const hm::ChainDev*)p)->gates; }
 const int32_t* hmtest_chain_env(const void* p) { return ((const hm::ChainDev*)p)->env_out; }
+int32_t* hmtest_chain_chi(const void* p) { return ((const hm::ChainDev*)p)->chi; }
 }

@@ -45,13 +45,17 @@ def host(tmp_path_factory):
            "hm_apply_ops": [vp, i64, vp, i32], "hm_query_memory": [P(binding.Params), P(ctypes.c_size_t)],
            "hmtest_launch": [ctypes.c_int] + [P(ctypes.c_int)] * 5,
            "hmtest_launch_chain": [ctypes.c_int, ctypes.c_int], "hmtest_chain_ints": [vp, P(i32)],
-           "hmtest_chain_ops": [vp], "hmtest_chain_gates": [vp], "hmtest_chain_env": [vp]}
+           "hmtest_chain_ops": [vp], "hmtest_chain_gates": [vp], "hmtest_chain_env": [vp],
+           "hmtest_chain_chi": [vp],
+           "hm_get_mps": [vp, i64, P(i32), i32, vp, ctypes.c_size_t, P(i32), P(ctypes.c_size_t)],
+           "hm_set_mps": [vp, i64, P(i32), i32, vp, ctypes.c_size_t, i32, i32]}
     for name, args in sig.items():
         getattr(lib, name).argtypes = args
     lib.hmtest_launch_chain.restype = vp
     lib.hmtest_chain_ops.restype = P(i32)
     lib.hmtest_chain_gates.restype = P(ctypes.c_double)
     lib.hmtest_chain_env.restype = P(i32)
+    lib.hmtest_chain_chi.restype = P(i32)
     return lib
 
 
@@ -260,4 +264,56 @@ def test_host_outputs_need_a_staging_block_device_outputs_do_not(host):
     dev = np.zeros(n_obs)                                # stands in for a caller's device buffer
     assert host.hm_measure_cluster_device(ctx.h, ptr, 1, dev.ctypes.data_as(ctypes.c_void_p), n_obs) == 0
     assert host.hm_collapse(ctx.h, ptr, 1, None, None) == 0
+    ctx.close()
+
+
+def _set(host, ctx, cid, dims, buf, centre=0, evolved=0, n_sites=None):
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+    b = np.ascontiguousarray(np.asarray(buf, dtype=np.float64))
+    return host.hm_set_mps(ctx.h, cid, d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                           len(d) - 1 if n_sites is None else n_sites, b.ctypes.data_as(ctypes.c_void_p),
+                           len(b), centre, evolved)
+
+
+def _get(host, ctx, cid, dims_cap=64, cap=None):
+    dims = np.zeros(dims_cap, dtype=np.int32)
+    n, nd = ctypes.c_int32(), ctypes.c_size_t()
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    rc = host.hm_get_mps(ctx.h, cid, dims.ctypes.data_as(P32), dims_cap, None, 0, ctypes.byref(n), ctypes.byref(nd))
+    if rc:
+        return rc, None, None
+    buf = np.zeros(max(nd.value if cap is None else cap, 1))
+    rc = host.hm_get_mps(ctx.h, cid, dims.ctypes.data_as(P32), dims_cap, buf.ctypes.data_as(ctypes.c_void_p),
+                         len(buf) if cap is None else cap, ctypes.byref(n), ctypes.byref(nd))
+    return rc, dims[: n.value + 1], buf[: nd.value]
+
+
+def test_mps_round_trip_and_its_argument_checks(host):
+    ctx = Ctx(host, 64 << 20)
+    p = binding.params(3, 2, beta=0.4, tau=0.1, chi_max=16)
+    where = {}
+    cid = _init_tracked(host, ctx, p, where)
+    desc = next(iter(where))
+    n = 8                                                   # Lx = 3, 2W = 2: 6 physical + 2 ancilla sites
+    dims = [1, 3, 9, 16, 16, 16, 9, 3, 1]
+    rng = np.random.default_rng(0)
+    buf = rng.standard_normal(sum(dims[s] * 3 * dims[s + 1] for s in range(n)))
+    assert _set(host, ctx, cid, dims, buf) == 0
+    rc, got_dims, got = _get(host, ctx, cid)
+    assert rc == 0 and list(got_dims) == dims and np.array_equal(got, buf)
+    too_big = list(dims)
+    too_big[3] = 17                                         # above chi_max
+    bad_cases = [
+        _set(host, ctx, cid, too_big, np.zeros(sum(too_big[s] * 3 * too_big[s + 1] for s in range(n)))),
+        _set(host, ctx, cid, dims, buf[:-1]),                # wrong length
+        _set(host, ctx, cid, dims, buf, centre=2),           # centre must be on site 0
+        _set(host, ctx, cid, [2] + dims[1:], np.zeros(10)),  # open boundary needs dim 1
+        _set(host, ctx, cid, dims, buf, n_sites=7),          # wrong site count
+    ]
+    assert bad_cases == [binding.HM_ERR_ARG] * 5
+    assert _get(host, ctx, cid, dims_cap=n)[0] == binding.HM_ERR_ARG       # dims buffer needs n + 1
+    assert _get(host, ctx, cid, cap=10)[0] == binding.HM_ERR_ARG           # tensor buffer too small
+    chi = np.ctypeslib.as_array(host.hmtest_chain_chi(desc), shape=(n + 1,))
+    chi[4] = 1000                                           # a corrupted bond dim on the "device"
+    assert _get(host, ctx, cid)[0] == binding.HM_ERR_NUMERIC
     ctx.close()
