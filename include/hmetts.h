@@ -84,7 +84,10 @@ typedef int64_t hm_chain;
  *   beta, tau     inverse temperature and Trotter step; M = floor(beta/(2 tau) + 1/2)
  *                 (at least 1 when beta > 0) steps of size beta/(2M) are taken
  *                 (Sec. I.A).
- *   chi_max       bond dimension cap of every truncated SVD (>= 1).
+ *   chi_max       bond dimension cap of every truncated SVD (>= 1; under
+ *                 HM_MIXED the largest cap must be <= 2150, the shared memory
+ *                 the binary32 evolve stages its column blocks in; larger
+ *                 caps are refused with HM_ERR_ARG at admission).
  *   cutoff        truncation error target: the smallest kept count whose
  *                 discarded weight sum s^2 / total s^2 <= cutoff (Sec. II).
  *   precision     HM_FP64 or HM_MIXED.

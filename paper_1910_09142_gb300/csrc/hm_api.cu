@@ -574,13 +574,27 @@ int hm_destroy(hm_ctx* ctx) {
   return HM_OK;
 }
 
+// Limits a chain's kernels place on its bond caps: the mixed evolve stages
+// column blocks in shared memory, so its footprint at the largest cap must
+// fit what one CTA may opt into.
+static int check_kernel_limits(const hm_params& p, const MemPlan& m, std::string* err) {
+  int bcols = 0;
+  if (p.precision == HM_MIXED && mixed_smem_bytes(m.chi_cap, &bcols) > kMaxSharedOptIn)
+    return fail(err, HM_ERR_ARG, "chi cap %d needs %zu bytes of shared memory in the mixed evolve (max %zu)",
+                m.chi_cap, mixed_smem_bytes(m.chi_cap, &bcols), kMaxSharedOptIn);
+  return HM_OK;
+}
+
 int hm_query_memory(const hm_params* p, size_t* bytes_out) {
   int rc = check_params(p, nullptr);
   if (rc) return rc;
   if (!bytes_out) return fail(nullptr, HM_ERR_ARG, "null output");
   const Layout L = make_layout(*p);
   const Schedule sc = make_schedule(L);
-  *bytes_out = mem_plan(*p, L, sc.ops.size(), sc.gates.size() / 81).total;
+  const MemPlan m = mem_plan(*p, L, sc.ops.size(), sc.gates.size() / 81);
+  rc = check_kernel_limits(*p, m, nullptr);
+  if (rc) return rc;
+  *bytes_out = m.total;
   return HM_OK;
 }
 
@@ -653,6 +667,11 @@ static int init_chain_impl(hm_ctx* ctx, const hm_params* p, const int8_t* env_in
     ch->cost += 4.0 * M * M * N + 8.0 * M * N * N + 9.0 * N * N * N;
   }
   ch->n_obs = 1 + 2 * (int)ch->L.meas.size();
+  rc = check_kernel_limits(*p, ch->mp, &ctx->err);
+  if (rc) {
+    delete ch;
+    return rc;
+  }
   {
     // at most 8 measured bonds may start on one site (measure kernel buffer)
     std::map<int, int> starts;

@@ -95,4 +95,23 @@ void set_global_error(const char* msg);
 // Mixed-precision evolve (hm_mixed.cu); chi_cap = largest bond cap in the batch.
 int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* stream);
 
+// Binary32 GEMM tile of the mixed evolve kernel, and the dynamic shared
+// memory one CTA may opt into on sm_100-class parts (227 KB).
+constexpr int kMixedGM = 64, kMixedGN = 64, kMixedGK = 16;
+constexpr size_t kMaxSharedOptIn = 227 * 1024;
+
+// Dynamic shared memory of the mixed evolve kernel at bond cap chi_cap: two
+// column blocks of b columns of the q + p <= 6 chi_cap row panel, plus the
+// cached column norms; b = 16, halved (down to 2) while that exceeds 210 KB.
+// The GEMM tile is the floor.  Writes b to *bcols.
+inline size_t mixed_smem_bytes(int chi_cap, int* bcols) {
+  const size_t qp = 6 * (size_t)chi_cap;
+  int b = 16;
+  while (b > 2 && (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float) > 210 * 1024) b /= 2;
+  *bcols = b;
+  const size_t bytes = (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float);
+  const size_t gemm = 2 * (size_t)kMixedGK * kMixedGM * sizeof(float);
+  return bytes > gemm ? bytes : gemm;
+}
+
 }  // namespace hm

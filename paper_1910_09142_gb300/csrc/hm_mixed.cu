@@ -26,7 +26,7 @@ namespace {
 
 constexpr int NT = 512;
 constexpr int kMaxSweeps = 60;
-constexpr int GM = 64, GN = 64, GK = 16;   // binary32 GEMM tile (512 threads, 2x4 outputs each)
+constexpr int GM = kMixedGM, GN = kMixedGN, GK = kMixedGK;   // binary32 GEMM tile (512 threads, 2x4 outputs each)
 
 struct Scal {
   double red[NT / 32][2];
@@ -556,17 +556,6 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
 }
 
 }  // namespace
-
-// Shared-memory bytes for column blocks of b columns at bond cap chi_cap.
-size_t mixed_smem_bytes(int chi_cap, int* bcols) {
-  const size_t qp = 6 * (size_t)chi_cap;        // q + p <= 3 chi + 3 chi
-  int b = 16;
-  while (b > 2 && (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float) > 210 * 1024) b /= 2;
-  *bcols = b;
-  size_t bytes = (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float);   // + cached column norms
-  const size_t gemm = 2 * GK * GM * sizeof(float);
-  return bytes > gemm ? bytes : gemm;
-}
 
 int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* stream) {
   if (b.n <= 0) return HM_OK;

@@ -174,3 +174,13 @@ def test_device_output_buffers_are_checked_before_any_launch():
     for t in (torch.zeros(6, dtype=torch.float64), np.zeros(6)):        # host memory
         with pytest.raises(ValueError):
             binding._device_buffer(t, torch.float64, 6, 0, "out")
+
+
+def test_mixed_precision_bond_cap_limit(lib):
+    """The binary32 evolve stages column blocks in shared memory: its largest
+    bond cap must fit 227 KB; FP64 has no such limit."""
+    assert binding.query_memory(binding.params(32, 8, chi_max=2048, precision=binding.HM_MIXED)) > 0
+    with pytest.raises(binding.HmError) as e:
+        binding.query_memory(binding.params(32, 8, chi_max=4096, precision=binding.HM_MIXED))
+    assert e.value.code == binding.HM_ERR_ARG
+    assert binding.query_memory(binding.params(32, 8, chi_max=4096)) > 0

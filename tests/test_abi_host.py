@@ -317,3 +317,10 @@ def test_mps_round_trip_and_its_argument_checks(host):
     chi[4] = 1000                                           # a corrupted bond dim on the "device"
     assert _get(host, ctx, cid)[0] == binding.HM_ERR_NUMERIC
     ctx.close()
+
+
+def test_admission_refuses_a_mixed_chain_beyond_the_shared_memory_plan(host):
+    ctx = Ctx(host, 1 << 20)
+    p = binding.params(32, 8, chi_max=4096, precision=binding.HM_MIXED)
+    assert ctx.init(p)[0] == binding.HM_ERR_ARG          # refused before any allocation
+    ctx.close()
