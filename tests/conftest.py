@@ -23,3 +23,16 @@ def lib():
     """The built C-ABI library (GPU tests only)."""
     from paper_1910_09142_gb300 import binding
     return binding.load()
+
+
+# Run order of the GPU files: the core parity tests (parity, mixed, serving,
+# susceptibility) first, then the tests of features layered on them (fused
+# schedule, resume, thermal averages), then the allocation-free entry point.
+# That entry point keeps a device array for the life of the process, so it
+# goes last. Under -x a failure in a later group still fails the run, but it
+# cannot keep an earlier group from running.
+_LATE = {"test_gpu_fused.py": 1, "test_gpu_resume.py": 1, "test_gpu_thermal.py": 1, "test_zz_no_alloc.py": 2}
+
+
+def pytest_collection_modifyitems(config, items):
+    items.sort(key=lambda it: _LATE.get(os.path.basename(str(it.fspath)), 0))    # stable
