@@ -77,3 +77,27 @@ def test_oracle_baseline_pool_uses_every_requested_core():
     rate, per_step, procs, wall = bench.oracle_parallel(2, procs=2, cfg=cfg)
     assert procs == 2 and len(per_step) == 2 and rate > 0 and wall > 0
     assert abs(rate - 4 / sum(per_step)) < 1e-12
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference on a tiny ladder: one JSON line with the
+    contract's keys (the oracle on host cores, steps bounded)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--Lx", "2", "--two-W", "2", "--chi-max", "8", "--beta", "0.2"],
+                       capture_output=True, text=True, timeout=300, cwd=root,
+                       env=dict(os.environ, RANK="0", WORLD_SIZE="1"))
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["config"]["Lx"] == 2 and line["config"]["schedule"] == "plain"
