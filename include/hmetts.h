@@ -108,6 +108,10 @@ typedef int64_t hm_chain;
  *                 Lx = 16, two_W = 8, chi = 256 ladder it runs 16% fewer
  *                 two-site splits, worth 5% of the dense-SVD flop count
  *                 (the fused splits are mostly small environment ones).
+ *   no_susceptibility 0: reserve the transfer workspace hm_measure_susceptibility
+ *                 needs, (20 + 4 |M|) chi_cap^2 doubles (about a fifth of a
+ *                 Lx = 16, chi = 256 chain); 1: do not, so more chains fit,
+ *                 and hm_measure_susceptibility refuses the chain (HM_ERR_ARG).
  */
 typedef struct {
   int32_t Lx, two_W;
@@ -120,6 +124,7 @@ typedef struct {
   int32_t basis_schedule;
   int32_t meas_col_lo, meas_col_hi;
   int32_t schedule;
+  int32_t no_susceptibility;
 } hm_params;
 
 /* Create a context on CUDA device `device`, sub-allocating from the caller's

@@ -53,16 +53,18 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("chain_id", ctypes.c_uint32), ("basis_schedule", ctypes.c_int32),
                 ("meas_col_lo", ctypes.c_int32), ("meas_col_hi", ctypes.c_int32),
-                ("schedule", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("no_susceptibility", ctypes.c_int32)]
 
 
 def params(Lx, two_W, J_leg=1.0, J_rung=1.0, beta=1.0, tau=0.05, chi_max=64, cutoff=1e-12,
-           precision=HM_FP64, seed=0, chain_id=0, basis_zx=True, meas_cols=None, schedule="plain"):
-    """``schedule``: "plain" / "fused" or HM_SCHED_PLAIN / HM_SCHED_FUSED."""
+           precision=HM_FP64, seed=0, chain_id=0, basis_zx=True, meas_cols=None, schedule="plain",
+           susceptibility=True):
+    """``schedule``: "plain" / "fused" or HM_SCHED_PLAIN / HM_SCHED_FUSED;
+    ``susceptibility=False`` skips the workspace of hm_measure_susceptibility."""
     lo, hi = (-1, -1) if meas_cols is None else meas_cols
     sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     return Params(Lx, two_W, J_leg, J_rung, beta, tau, chi_max, cutoff, precision, seed, chain_id,
-                  HM_ZX_ALTERNATE if basis_zx else HM_Z_ONLY, lo, hi, sched)
+                  HM_ZX_ALTERNATE if basis_zx else HM_Z_ONLY, lo, hi, sched, 0 if susceptibility else 1)
 
 
 _lib = None

@@ -69,6 +69,8 @@ int check_params(const hm_params* p, std::string* err) {
     return fail(err, HM_ERR_ARG, "unknown basis schedule");
   if (p->schedule != HM_SCHED_PLAIN && p->schedule != HM_SCHED_FUSED)
     return fail(err, HM_ERR_ARG, "unknown op schedule %d", p->schedule);
+  if (p->no_susceptibility != 0 && p->no_susceptibility != 1)
+    return fail(err, HM_ERR_ARG, "no_susceptibility must be 0 or 1");
   const bool dflt = p->meas_col_lo == -1 && p->meas_col_hi == -1;
   if (!dflt && (p->meas_col_lo < 0 || p->meas_col_hi > p->Lx || p->meas_col_lo >= p->meas_col_hi))
     return fail(err, HM_ERR_ARG, "measured columns must satisfy 0 <= lo < hi <= Lx");
@@ -323,6 +325,9 @@ struct MemPlan {
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
+// chi_cap x chi_cap matrices the susceptibility kernel keeps in env_ws.
+int64_t susceptibility_matrices(const Layout& L) { return 20 + 4 * (int64_t)L.region.size(); }
+
 MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gates) {
   MemPlan m;
   const int n = L.n_sites;
@@ -349,8 +354,8 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gat
   for (const Bond& b : L.meas)
     if (std::find(ends.begin(), ends.end(), b.j) == ends.end()) ends.push_back(b.j);
   // the susceptibility sweeps use 20 matrices + 4 stored per region site
-  m.env_cap = std::max<int64_t>(10 + (int64_t)ends.size(), 20 + 4 * (int64_t)L.region.size()) * m.chi_cap *
-              m.chi_cap;
+  const int64_t sus = p.no_susceptibility ? 0 : susceptibility_matrices(L);
+  m.env_cap = std::max<int64_t>(10 + (int64_t)ends.size(), sus) * m.chi_cap * m.chi_cap;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -909,8 +914,12 @@ int hm_measure_susceptibility(hm_ctx* ctx, const hm_chain* ids, int32_t n, doubl
   std::vector<Chain*> cs;
   int rc = lookup(ctx, ids, n, &cs);
   if (rc) return rc;
-  for (Chain* c : cs)
+  for (Chain* c : cs) {
     if (c->phase != 1) return fail(&ctx->err, HM_ERR_STATE, "the susceptibility needs an evolved chain");
+    // the kernel assumes its workspace: never launch it on a chain without one
+    if (c->mp.env_cap < susceptibility_matrices(c->L) * c->mp.chi_cap * c->mp.chi_cap)
+      return fail(&ctx->err, HM_ERR_ARG, "chain was created with no_susceptibility = 1");
+  }
   HM_CUDA(ctx, cudaSetDevice(ctx->device));
   Scratch sc{ctx};
   rc = sc.get((size_t)n * sizeof(double));

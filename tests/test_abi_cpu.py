@@ -184,3 +184,15 @@ def test_mixed_precision_bond_cap_limit(lib):
         binding.query_memory(binding.params(32, 8, chi_max=4096, precision=binding.HM_MIXED))
     assert e.value.code == binding.HM_ERR_ARG
     assert binding.query_memory(binding.params(32, 8, chi_max=4096)) > 0
+
+
+def test_susceptibility_workspace_is_optional(lib):
+    full = binding.query_memory(binding.params(16, 8, chi_max=256, cutoff=1e-7))
+    lean = binding.query_memory(binding.params(16, 8, chi_max=256, cutoff=1e-7, susceptibility=False))
+    # the workspace holds (20 + 4 |M|) chi^2 doubles, |M| = 8 cluster sites, instead of the
+    # measurement's 10 + (measured end sites): about a fifth of this chain
+    assert 0.15 * full < full - lean < 0.25 * full
+    p = binding.params(4, 4)
+    p.no_susceptibility = 2
+    with pytest.raises(binding.HmError):
+        binding.num_obs(p)

@@ -324,3 +324,20 @@ def test_admission_refuses_a_mixed_chain_beyond_the_shared_memory_plan(host):
     p = binding.params(32, 8, chi_max=4096, precision=binding.HM_MIXED)
     assert ctx.init(p)[0] == binding.HM_ERR_ARG          # refused before any allocation
     ctx.close()
+
+
+def test_susceptibility_is_refused_on_a_chain_without_its_workspace(host):
+    host.hm_measure_susceptibility.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                               ctypes.c_void_p]
+    ctx = Ctx(host, 256 << 20)
+    out = np.zeros(2)
+    for sus, want in ((True, 0), (False, binding.HM_ERR_ARG)):
+        _, cid = ctx.init(binding.params(3, 2, beta=0.4, tau=0.1, chi_max=16, susceptibility=sus))
+        a, ptr = ctx.ids([cid])
+        assert host.hm_evolve(ctx.h, ptr, 1) == 0
+        host.hmtest_clear()
+        assert host.hm_measure_susceptibility(ctx.h, ptr, 1, out.ctypes.data_as(ctypes.c_void_p)) == want
+        kinds = [l["kind"] for l in _launches(host)]
+        assert kinds == ([K_SUSCEPT] if sus else [])          # never launched without the workspace
+        assert host.hm_free_chain(ctx.h, cid) == 0
+    ctx.close()
