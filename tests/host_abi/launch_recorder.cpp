@@ -1,37 +1,15 @@
-// TEST INFRASTRUCTURE: a host-only stand-in for the CUDA runtime and the
-// kernel launchers, so the host side of the C ABI (hm_api.cu: parameter
-// checks, planner, chain image, arena, state machine, batching) can be
-// exercised on a machine without a GPU.  "Device" memory is host memory,
-// copies are memcpy, and each launcher only records what it was handed.
-// Nothing here computes any step of the method; the product library never
-// links it.
-#include <cuda_runtime_api.h>
-
+// TEST INFRASTRUCTURE: stand-ins for the kernel launchers, so the host side
+// of the C ABI (hm_api.cu: parameter checks, planner, chain image, arena,
+// state machine, batching) can be exercised on a machine without a GPU.
+// Each launcher only records what it was handed (the runtime calls are in
+// cuda_runtime_stub.cpp).  Nothing here computes any step of the method;
+// the product library never links it.
 #include <cstring>
 #include <vector>
 
 #include "../../paper_1910_09142_gb300/csrc/hm_internal.h"
 
-extern "C" {
 
-cudaError_t cudaSetDevice(int) { return cudaSuccess; }
-cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
-cudaError_t cudaGetLastError(void) { return cudaSuccess; }
-const char* cudaGetErrorString(cudaError_t) { return "stub"; }
-cudaError_t cudaMemcpy(void* dst, const void* src, size_t n, enum cudaMemcpyKind) {
-  std::memmove(dst, src, n);
-  return cudaSuccess;
-}
-cudaError_t cudaMemcpyAsync(void* dst, const void* src, size_t n, enum cudaMemcpyKind, cudaStream_t) {
-  std::memmove(dst, src, n);
-  return cudaSuccess;
-}
-cudaError_t cudaMemsetAsync(void* dst, int v, size_t n, cudaStream_t) {
-  std::memset(dst, v, n);
-  return cudaSuccess;
-}
-
-}  // extern "C"
 
 namespace {
 enum Kind { K_EVOLVE64 = 0, K_EVOLVE_MIXED, K_MEASURE, K_COLLAPSE, K_RESET, K_SUSCEPT };

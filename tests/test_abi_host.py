@@ -1,7 +1,7 @@
 """The host side of the C ABI, run on the CPU (no GPU).
 
-``hm_api.cu`` is compiled as plain C++ with a test-only stand-in for the
-CUDA runtime and the kernel launchers (``tests/host_abi/cuda_stub.cpp``).
+``hm_api.cu`` is compiled as plain C++ with test-only stand-ins for the
+CUDA runtime and the kernel launchers (``tests/host_abi/``).
 Device memory is host memory, and each launcher records the batch it was
 handed. The tests read back what the kernels would receive: the chain image
 (op list, gate table, counters, environment), the launch order and batch
@@ -30,8 +30,9 @@ def host(tmp_path_factory):
         pytest.skip("needs g++ and the CUDA headers")
     out = str(tmp_path_factory.mktemp("host_abi") / "libhm_host.so")
     src = [os.path.join(ROOT, "paper_1910_09142_gb300", "csrc", "hm_api.cu"),
-           os.path.join(ROOT, "tests", "host_abi", "cuda_stub.cpp")]
-    r = subprocess.run([cxx, "-std=c++17", "-O1", "-shared", "-fPIC", "-x", "c++", src[0], "-x", "c++", src[1],
+           os.path.join(ROOT, "tests", "host_abi", "cuda_runtime_stub.cpp"),
+           os.path.join(ROOT, "tests", "host_abi", "launch_recorder.cpp")]
+    r = subprocess.run([cxx, "-std=c++17", "-O1", "-shared", "-fPIC", "-x", "c++", *src,
                         "-I" + inc, "-o", out, "-ldl", "-Wl,-Bsymbolic"],   # the stub, not a loaded cudart
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr

@@ -1,0 +1,178 @@
+"""The library's CUDA kernels, run on the CPU, against the oracle (no GPU).
+
+``tests/simt/`` compiles ``hm_fp64.cu`` and ``hm_mixed.cu`` as host C++.
+Each block's threads are cooperative fibers, __syncthreads and warp
+shuffles keep their meaning, and the launches run through the unchanged host
+code of ``hm_api.cu``. What runs is the kernel source itself, so these tests
+check its logic (indexing, truncation, Philox draws, collapse, reset,
+counters) at the GPU parity bars. They do not check GB300 behaviour (timing,
+memory model, rounding of the FMA contraction); the ``-m gpu`` tests do.
+
+Tiny chains keep each sample to seconds: Lx = 2, one cluster column,
+beta = 0.2 (one Trotter step).
+"""
+import ctypes
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import chain as ochain
+from oracle import measure as omeasure
+from oracle import mps as omps
+from paper_1910_09142_gb300 import binding
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "simt"))
+import build_emulated  # noqa: E402
+
+pytestmark = pytest.mark.slow
+
+CFG = dict(Lx=2, two_W=2, J_leg=1.0, J_rung=0.7, beta=0.2, tau=0.1, chi_max=16, cutoff=1e-12)
+RTOL, ATOL = 1e-10, 1e-12
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    try:
+        path = build_emulated.build(str(tmp_path_factory.mktemp("simt")))
+    except FileNotFoundError as e:
+        pytest.skip(str(e))
+    lib = ctypes.CDLL(path)
+    P, vp, i32, i64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {"hm_create": [P(vp), ctypes.c_int, vp, ctypes.c_size_t, vp], "hm_destroy": [vp],
+           "hm_init_chain": [vp, P(binding.Params), vp, P(i64)],
+           "hm_resume_chain": [vp, P(binding.Params), vp, i64, P(i64)],
+           "hm_free_chain": [vp, i64], "hm_evolve": [vp, P(i64), i32],
+           "hm_measure_cluster": [vp, P(i64), i32, vp, i32], "hm_collapse": [vp, P(i64), i32, vp, vp],
+           "hm_measure_susceptibility": [vp, P(i64), i32, vp],
+           "hm_get_mps": [vp, i64, P(i32), i32, vp, ctypes.c_size_t, P(i32), P(ctypes.c_size_t)],
+           "hm_last_error": [vp]}
+    for name, args in sig.items():
+        getattr(lib, name).argtypes = args
+    lib.hm_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+class Emu:
+    """A context over host memory; chains advance one Markov step at a time."""
+
+    def __init__(self, lib, nbytes=64 << 20):
+        self.lib = lib
+        self.mem = np.zeros(nbytes + 256, dtype=np.uint8)
+        base = self.mem.ctypes.data + (-self.mem.ctypes.data) % 256
+        self.h = ctypes.c_void_p()
+        assert lib.hm_create(ctypes.byref(self.h), 0, ctypes.c_void_p(base), nbytes, None) == 0
+
+    def _ok(self, rc):
+        assert rc == 0, (rc, self.lib.hm_last_error(self.h))
+
+    def init(self, p, env=None, n=0):
+        out = ctypes.c_int64()
+        e = None if env is None else np.ascontiguousarray(np.asarray(env, dtype=np.int8))
+        ptr = None if e is None else e.ctypes.data_as(ctypes.c_void_p)
+        self._ok(self.lib.hm_resume_chain(self.h, ctypes.byref(p), ptr, n, ctypes.byref(out)) if n
+                 else self.lib.hm_init_chain(self.h, ctypes.byref(p), ptr, ctypes.byref(out)))
+        return out.value
+
+    def _ids(self, cid):
+        self._a = np.array([cid], dtype=np.int64)
+        return self._a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+    def evolve(self, cid):
+        self._ok(self.lib.hm_evolve(self.h, self._ids(cid), 1))
+
+    def measure(self, cid, p):
+        out = np.zeros(binding.num_obs(p))
+        self._ok(self.lib.hm_measure_cluster(self.h, self._ids(cid), 1, out.ctypes.data_as(ctypes.c_void_p),
+                                             len(out)))
+        return out
+
+    def collapse(self, cid, p):
+        n_env = binding.num_env(p)
+        env, lp = np.zeros(max(n_env, 1), dtype=np.int8), np.zeros(1)
+        self._ok(self.lib.hm_collapse(self.h, self._ids(cid), 1, env.ctypes.data_as(ctypes.c_void_p),
+                                      lp.ctypes.data_as(ctypes.c_void_p)))
+        return list(env[:n_env]), float(lp[0])
+
+    def sample(self, cid, p):
+        self.evolve(cid)
+        obs = self.measure(cid, p)
+        env, lp = self.collapse(cid, p)
+        return obs, env, lp
+
+    def mps(self, cid):
+        dims = np.zeros(64, dtype=np.int32)
+        n, nd = ctypes.c_int32(), ctypes.c_size_t()
+        P32 = ctypes.POINTER(ctypes.c_int32)
+        self._ok(self.lib.hm_get_mps(self.h, cid, dims.ctypes.data_as(P32), 64, None, 0, ctypes.byref(n),
+                                     ctypes.byref(nd)))
+        buf = np.zeros(nd.value)
+        self._ok(self.lib.hm_get_mps(self.h, cid, dims.ctypes.data_as(P32), 64, buf.ctypes.data_as(ctypes.c_void_p),
+                                     len(buf), ctypes.byref(n), ctypes.byref(nd)))
+        out, o = [], 0
+        for s in range(n.value):
+            size = dims[s] * 3 * dims[s + 1]
+            out.append(buf[o:o + size].reshape(dims[s], 3, dims[s + 1]))
+            o += size
+        return out
+
+    def close(self):
+        self.lib.hm_destroy(self.h)
+
+
+def _same_state(a, b, tol=1e-10):
+    va, vb = omps.MPS(a).to_dense(), omps.MPS(b).to_dense()
+    return np.abs(va - np.sign(va @ vb) * vb).max() < tol
+
+
+@pytest.mark.parametrize("schedule", ["plain", "fused"])
+def test_fp64_kernels_match_the_oracle(emu, schedule):
+    """Evolved state, observables, outcomes and log p of two samples."""
+    e = Emu(emu)
+    p = binding.params(**CFG, seed=3, chain_id=1, schedule=schedule)
+    cid = e.init(p)
+    ref = ochain.HybridChain(seed=3, chain_id=1, schedule=schedule, **CFG)
+    for step in range(2):
+        e.evolve(cid)
+        if step == 0:
+            assert _same_state(e.mps(cid), ref.evolve().tensors)
+        obs = e.measure(cid, p)
+        env, lp = e.collapse(cid, p)
+        r = ref.sample()
+        assert np.allclose(obs, r["obs"], rtol=RTOL, atol=ATOL)
+        assert env == r["env_out"] and abs(lp - r["logp"]) < 1e-9
+    e.close()
+
+
+def test_resume_through_the_kernels_repeats_the_chain(emu):
+    """Resume after sample 1 (read in the S^x basis): the reset kernel builds
+    the initial state from the preset counters, and sample 2 is bit-identical."""
+    e = Emu(emu)
+    p = binding.params(**CFG, seed=8, chain_id=2, precision=binding.HM_MIXED)
+    cid = e.init(p)
+    recs = [e.sample(cid, p) for _ in range(3)]
+    again = e.init(p, recs[1][1], 2)
+    obs, env, lp = e.sample(again, p)
+    assert np.array_equal(obs, recs[2][0]) and env == recs[2][1] and lp == recs[2][2]
+    # the binary32 path within its stated tolerance of the oracle
+    ref = ochain.HybridChain(seed=8, chain_id=2, **CFG)
+    r = ref.sample()
+    assert abs(recs[0][0][0] - r["obs"][0]) < 1e-3 * abs(r["obs"][0])
+    assert np.abs(recs[0][0][1:] - r["obs"][1:]).max() < 2e-3
+    e.close()
+
+
+def test_susceptibility_kernel_matches_the_oracle(emu):
+    e = Emu(emu)
+    p = binding.params(**CFG, seed=5)
+    cid = e.init(p)
+    e.evolve(cid)
+    out = np.zeros(2)
+    e._ok(emu.hm_measure_susceptibility(e.h, e._ids(cid), 1, out.ctypes.data_as(ctypes.c_void_p)))
+    ref = ochain.HybridChain(seed=5, **CFG)
+    lad = ref.ladder
+    region = sorted({k for i, j, _ in ref.meas_bonds for k in (i, j)})
+    chi, raw = omeasure.susceptibility(ref.evolve(), lad, region, CFG["beta"])
+    assert abs(out[1] - raw) < 1e-10 * max(1.0, abs(raw)) and abs(out[0] - chi) < 1e-10 * max(1.0, abs(chi))
+    e.close()
