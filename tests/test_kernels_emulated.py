@@ -176,3 +176,25 @@ def test_susceptibility_kernel_matches_the_oracle(emu):
     chi, raw = omeasure.susceptibility(ref.evolve(), lad, region, CFG["beta"])
     assert abs(out[1] - raw) < 1e-10 * max(1.0, abs(raw)) and abs(out[0] - chi) < 1e-10 * max(1.0, abs(chi))
     e.close()
+
+
+@pytest.mark.parametrize("cfg,precision", [
+    (dict(Lx=1, two_W=2, beta=0.3), binding.HM_FP64),       # single rung, pure ancilla
+    (dict(Lx=1, two_W=0, beta=0.3), binding.HM_FP64),       # single rung, METTS
+    (dict(Lx=2, two_W=2, beta=0.0), binding.HM_FP64),       # no evolution at all
+    (dict(Lx=1, two_W=2, beta=0.3), binding.HM_MIXED),
+    (dict(Lx=2, two_W=2, beta=0.0), binding.HM_MIXED),
+])
+def test_edge_cases_match_the_oracle(emu, cfg, precision):
+    full = dict(J_leg=1.0, J_rung=0.7, tau=0.1, chi_max=16, cutoff=1e-12, **cfg)
+    e = Emu(emu)
+    p = binding.params(**full, seed=4, chain_id=2, precision=precision)
+    cid = e.init(p)
+    ref = ochain.HybridChain(seed=4, chain_id=2, **full)
+    tol = 1e-10 if precision == binding.HM_FP64 else 1e-6
+    for _ in range(2):
+        obs, env, _ = e.sample(cid, p)
+        r = ref.sample()
+        assert np.abs(obs - r["obs"]).max() <= tol * max(1.0, np.abs(r["obs"]).max())
+        assert env == r["env_out"]
+    e.close()
