@@ -9,8 +9,6 @@
 
 #include "../../paper_1910_09142_gb300/csrc/hm_internal.h"
 
-
-
 namespace {
 enum Kind { K_EVOLVE64 = 0, K_EVOLVE_MIXED, K_MEASURE, K_COLLAPSE, K_RESET, K_SUSCEPT };
 struct Launch {
