@@ -8,11 +8,20 @@
 // returns leaves the barriers it would have joined.  If no fiber can run and
 // no barrier can open, the block's barriers do not match: the launch stops
 // with a message instead of hanging.  Fibers make a run deterministic.
+//
+// SIMT_ORDER picks the order in which runnable fibers run within a phase:
+// "forward" (default), "reverse", or "random:<seed>" (a new permutation on
+// every pass).  A kernel without data races gives bit-identical results in
+// every order, because nothing orders two threads between barriers; a
+// result that changes with the order exposes a missing barrier.
 #include <ucontext.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <memory>
+#include <numeric>
 #include <vector>
 
 #include "simt_prelude.h"
@@ -98,7 +107,36 @@ uint64_t exchange(uint64_t bits, int lane_xor) {
 }
 void* dynamic_smem() { return g_smem.data(); }
 
+// Fiber order of one pass: forward, reversed, or a fresh pseudorandom
+// permutation (a 64-bit linear congruential generator, Knuth's MMIX constants).
+struct Order {
+  int mode = 0;                       // 0 forward, 1 reverse, 2 random
+  uint64_t state = 0;
+  std::vector<unsigned> idx;
+  void init(unsigned n) {
+    const char* e = std::getenv("SIMT_ORDER");
+    mode = 0;
+    if (e && std::strcmp(e, "reverse") == 0) mode = 1;
+    if (e && std::strncmp(e, "random:", 7) == 0) {
+      mode = 2;
+      state = std::strtoull(e + 7, nullptr, 10) * 2 + 1;
+    }
+    idx.resize(n);
+    std::iota(idx.begin(), idx.end(), 0u);
+    if (mode == 1) std::reverse(idx.begin(), idx.end());
+  }
+  void next_pass() {
+    if (mode != 2) return;
+    for (size_t i = idx.size(); i > 1; --i) {          // Fisher-Yates
+      state = state * 6364136223846793005ULL + 1442695040888963407ULL;
+      std::swap(idx[i - 1], idx[(state >> 33) % i]);
+    }
+  }
+};
+
 void launch(unsigned grid, unsigned block, size_t smem, const std::function<void()>& body) {
+  Order order;
+  order.init(block);
   g_bdim = {block, 1, 1};
   g_gdim = {grid, 1, 1};
   g_smem.assign(smem + 16, 0);
@@ -121,7 +159,9 @@ void launch(unsigned grid, unsigned block, size_t smem, const std::function<void
     }
     for (;;) {
       bool ran = false, live = false;
-      for (Fiber& f : g_fibers) {
+      order.next_pass();
+      for (unsigned i : order.idx) {
+        Fiber& f = g_fibers[i];
         if (f.state == DONE) continue;
         live = true;
         if (f.state != RUNNABLE) continue;

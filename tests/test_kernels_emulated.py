@@ -198,3 +198,35 @@ def test_edge_cases_match_the_oracle(emu, cfg, precision):
         assert np.abs(obs - r["obs"]).max() <= tol * max(1.0, np.abs(r["obs"]).max())
         assert env == r["env_out"]
     e.close()
+
+
+@pytest.mark.parametrize("precision,order", [(binding.HM_FP64, "reverse"), (binding.HM_MIXED, "random:7")])
+def test_results_do_not_depend_on_thread_order(emu, precision, order):
+    """A race check: nothing orders two threads of a block between barriers,
+    so a kernel without data races gives bit-identical results whatever
+    order its threads run in.  One Markov step in the default order, then
+    the same step with the threads of every phase reversed or shuffled:
+    states, observables, outcomes and log p must match exactly."""
+    def run():
+        e = Emu(emu)
+        p = binding.params(**CFG, seed=6, chain_id=3, precision=precision)
+        cid = e.init(p)
+        e.evolve(cid)
+        state = e.mps(cid)
+        obs = e.measure(cid, p)
+        env, lp = e.collapse(cid, p)
+        e.close()
+        return state, obs, env, lp
+    old = os.environ.get("SIMT_ORDER")
+    try:
+        os.environ["SIMT_ORDER"] = "forward"
+        a = run()
+        os.environ["SIMT_ORDER"] = order
+        b = run()
+    finally:
+        if old is None:
+            os.environ.pop("SIMT_ORDER", None)
+        else:
+            os.environ["SIMT_ORDER"] = old
+    assert all(np.array_equal(x, y) for x, y in zip(a[0], b[0]))
+    assert np.array_equal(a[1], b[1]) and a[2] == b[2] and a[3] == b[3]
