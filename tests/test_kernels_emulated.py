@@ -230,3 +230,36 @@ def test_results_do_not_depend_on_thread_order(emu, precision, order):
             os.environ["SIMT_ORDER"] = old
     assert all(np.array_equal(x, y) for x, y in zip(a[0], b[0]))
     assert np.array_equal(a[1], b[1]) and a[2] == b[2] and a[3] == b[3]
+
+
+def test_allocation_free_update_matches_the_oracle_split(emu):
+    """hm_two_site_update_static (its scratch is a file-scope device array,
+    here host memory): the truncated two-site product equals the oracle's
+    split of the same tensors, and the kept side is an isometry."""
+    from oracle import model
+    emu.hm_two_site_update_static.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int32] * 3 + [
+        ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32] + [ctypes.c_void_p] * 4
+    rng = np.random.default_rng(11)
+    chi_l, chi_m, chi_r, chi_max, cutoff = 4, 6, 5, 7, 1e-12
+    A = rng.standard_normal((chi_l, 3, chi_m))
+    B = rng.standard_normal((chi_m, 3, chi_r))
+    gate = model.bond_gate(0.05)
+    for absorb in (model.ABSORB_L, model.ABSORB_R):
+        kmax = min(3 * chi_l, 3 * chi_r, chi_max)
+        oA, oB = np.full(chi_l * 3 * kmax, np.nan), np.full(kmax * 3 * chi_r, np.nan)
+        kk = np.zeros(1, dtype=np.int32)
+        g = np.ascontiguousarray(gate.reshape(-1))
+        rc = emu.hm_two_site_update_static(A.ctypes.data, B.ctypes.data, chi_l, chi_m, chi_r, g.ctypes.data,
+                                           chi_max, cutoff, absorb, oA.ctypes.data, oB.ctypes.data,
+                                           kk.ctypes.data, None)
+        assert rc == 0
+        k = int(kk[0])
+        st = omps.MPS([A.copy(), B.copy()], 0 if absorb == model.ABSORB_L else 1)
+        st.centre = 0
+        omps.split(st, 0, gate, absorb, chi_max, cutoff)
+        assert k == st.tensors[0].shape[2]
+        got = oA[: chi_l * 3 * k].reshape(-1, k) @ oB[: k * 3 * chi_r].reshape(k, -1)
+        want = st.tensors[0].reshape(-1, k) @ st.tensors[1].reshape(k, -1)
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+        iso = oB[: k * 3 * chi_r].reshape(k, -1) if absorb == model.ABSORB_L else oA[: chi_l * 3 * k].reshape(-1, k).T
+        assert np.abs(iso @ iso.T - np.eye(k)).max() < 1e-12
