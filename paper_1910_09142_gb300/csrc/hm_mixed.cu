@@ -17,6 +17,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "hm_internal.h"
 
@@ -561,15 +562,20 @@ int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* s
   if (b.n <= 0) return HM_OK;
   int bcols = 16;
   const size_t smem = mixed_smem_bytes(chi_cap, &bcols);
-  // the shared-memory opt-in is per device: cache it per device ordinal
+  // the shared-memory opt-in is per device: cache it per device ordinal,
+  // under a lock (serving workers may launch from several host threads)
+  static std::mutex mu;
   static size_t configured[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HM_ERR_CUDA;
-  if (dev < 0 || dev >= 64 || smem > configured[dev]) {
-    if (cudaFuncSetAttribute(evolve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return HM_ERR_CUDA;
-    if (dev >= 0 && dev < 64) configured[dev] = smem;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || smem > configured[dev]) {
+      if (cudaFuncSetAttribute(evolve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return HM_ERR_CUDA;
+      if (dev >= 0 && dev < 64) configured[dev] = smem;
+    }
   }
   evolve_mixed_kernel<<<b.n, NT, smem, (cudaStream_t)stream>>>(b, o, bcols);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;

@@ -2,13 +2,15 @@
 
 The fused schedule changes only the op list and the gate table the kernels
 read, so the plain schedule's bars apply. FP64: per-sample observables at
-1e-10 relative, collapse outcomes bit-exact, log-probabilities at 1e-9,
-and states at 1e-10 as dense vectors up to sign. The state check is made
+1e-10 relative, collapse outcomes bit-exact, log-probabilities at 1e-10
+relative, and states at 1e-10 as dense vectors up to sign. The state check is made
 only where the state is stable under rounding. On the Lx=4, 2W=4, beta=2,
 chi=64 chain about 300 splits cut at the chi cap between close singular
 values. There a 1e-16 relative change of the gates moves the oracle's own
 dense state by 1e-9 (fused) to 1e-8 (plain), and its observables by only
-2e-14. Mixed: the stated 1e-3 / 2e-3. Without truncation the fused and
+2e-14, and its collapse log-probability by more than 1e-9
+(``test_logp_moves_under_gate_rounding_at_the_chi_cap``): that chain's
+log p is compared at 2e-8 absolute. Mixed: the stated 1e-3 / 2e-3. Without truncation the fused and
 the plain evolution reach the same state.
 """
 import numpy as np
@@ -20,6 +22,7 @@ from oracle import mps as omps
 pytestmark = pytest.mark.gpu
 
 RTOL, ATOL = 1e-10, 1e-12
+LOGP_CHI_CAP = 2e-8   # pinned by test_logp_moves_under_gate_rounding_at_the_chi_cap
 
 CFGS = [
     dict(Lx=3, two_W=2, J_leg=1.0, J_rung=0.5, beta=0.6, tau=0.1, chi_max=64, cutoff=1e-12),
@@ -70,7 +73,8 @@ def test_fused_samples_match_oracle(ctx):
                     assert _same_state(got, ref.last_mps.tensors), q
                 assert np.allclose(obs, r["obs"], rtol=RTOL, atol=ATOL), (q, obs, r["obs"])
                 assert list(env[0]) == r["env_out"]
-                assert abs(logp[0] - r["logp"]) < 1e-9
+                bar = 1e-10 * max(1.0, abs(r["logp"])) if state_stable[q] else LOGP_CHI_CAP
+                assert abs(logp[0] - r["logp"]) <= bar, (q, logp[0], r["logp"])
     finally:
         for cid in ids:
             ctx.free_chain(cid)

@@ -1,7 +1,7 @@
 """CUDA path vs the FP64 oracle, through the C ABI (GPU tests).
 
 Tolerances (FP64 path): per-sample observables within 1e-10 relative (1e-12
-absolute floor); collapse outcomes bit-exact; log-probabilities within 1e-9;
+absolute floor); collapse outcomes bit-exact; log-probabilities within 1e-10 relative;
 states compared as dense vectors up to the global sign at 1e-10.
 """
 import math
@@ -16,6 +16,7 @@ from oracle import mps as omps
 pytestmark = pytest.mark.gpu
 
 RTOL, ATOL = 1e-10, 1e-12
+LOGP_CHI_CAP = 2e-8   # pinned by test_logp_moves_under_gate_rounding_at_the_chi_cap
 
 
 @pytest.fixture(scope="module")
@@ -89,7 +90,7 @@ def test_samples_match_oracle(ctx):
                 r = ref.sample()
                 assert np.allclose(obs, r["obs"], rtol=RTOL, atol=ATOL), (obs, r["obs"])
                 assert list(env[0]) == r["env_out"]
-                assert abs(logp[0] - r["logp"]) < 1e-9
+                assert abs(logp[0] - r["logp"]) <= 1e-10 * max(1.0, abs(r["logp"]))
     finally:
         for cid in ids:
             ctx.free_chain(cid)
@@ -113,6 +114,9 @@ def test_small_config_samples(ctx):
             worst = max(worst, abs(obs[0] - r["obs"][0]) / abs(r["obs"][0]))
             assert np.allclose(obs, r["obs"], rtol=RTOL, atol=ATOL)
             assert list(env[0]) == r["env_out"]
+            # chi-capped chain: its log p moves by ~5e-10 under rounding alone
+            # (test_logp_moves_under_gate_rounding_at_the_chi_cap)
+            assert abs(logp[0] - r["logp"]) <= LOGP_CHI_CAP
         assert worst < RTOL
     finally:
         ctx.free_chain(cid)

@@ -209,3 +209,37 @@ def test_observables_stable_under_gate_rounding_at_the_chi_cap():
     g2 = [g * (1 + 1e-16 * rng.standard_normal(g.shape)) for g in ch.gates]
     obs = measure.measure(mps.evolve(ch.initial_mps(), ch.ops, g2, 64, 1e-12), ch.meas_bonds)
     assert np.max(np.abs(obs - ref) / np.maximum(np.abs(ref), 1e-2)) < 1e-12
+
+
+
+@pytest.mark.parametrize("schedule, seed, chain_id, trials", [
+    (model.SCHEDULE_FUSED, 5, 1, (11, 14)),
+    (model.SCHEDULE_PLAIN, 0, 0, (1, 3)),
+])
+def test_logp_moves_under_gate_rounding_at_the_chi_cap(schedule, seed, chain_id, trials):
+    """Lx=4, 2W=4, beta=2, chi=64 (the small workload), sample 1: a 1e-16
+    relative change of every gate moves the oracle's own collapse
+    log-probability by more than 1e-10 relative (the cut falls between
+    close singular values; the fused chain moves by more than 1e-9).  So a
+    1e-10 relative bar on log p is below the method's rounding noise on
+    these chains.  The GPU tests compare their log p at 2e-8 absolute,
+    above every deviation seen here, and every other chain's at 1e-10
+    relative."""
+    from oracle import chain
+    cfg = dict(Lx=4, two_W=4, J_leg=1.0, J_rung=1.0, beta=2.0, tau=0.1, chi_max=64, cutoff=1e-12)
+    ch = chain.HybridChain(seed=seed, chain_id=chain_id, schedule=schedule, **cfg)
+    ch.sample()
+    env, basis_in, n = list(ch.env), ch.env_basis, ch.n
+    ref = ch.sample()
+    dev = []
+    for trial in trials:
+        rng = np.random.default_rng(trial)
+        g2 = [g * (1 + 1e-16 * rng.standard_normal(g.shape)) for g in ch.gates]
+        st = mps.evolve(mps.MPS(collapse.product_state(ch.ladder, env, basis_in), 0), ch.ops, g2, 64, 1e-12)
+        out, logp, _ = collapse.collapse(st, ch.ladder, collapse.sample_basis(n, True), seed, chain_id, n)
+        assert list(out) == ref["env_out"]
+        dev.append(abs(logp - ref["logp"]))
+    assert max(dev) > 1e-10 * abs(ref["logp"])
+    if schedule == model.SCHEDULE_FUSED:
+        assert max(dev) > 1e-9
+    assert max(dev) < 5e-9
