@@ -67,6 +67,8 @@ extern "C" {
 #define HM_ZX_ALTERNATE 0    /* collapse sample n in the Sz basis (n even) or Sx basis (n odd) */
 #define HM_Z_ONLY 1          /* collapse every sample in the Sz basis              */
 
+#define HM_NUM_STATS 12      /* doubles written by hm_chain_stats                   */
+
 #define HM_SCHED_PLAIN 0     /* every gate and SWAP of the schedule is its own split */
 #define HM_SCHED_FUSED 1     /* consecutive splits on one site pair become one split */
                              /* with the product gate; SWAP SWAP pairs drop out      */
@@ -207,14 +209,21 @@ int hm_collapse(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, do
 int hm_collapse_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out_dev,
                        double* logp_out_dev);
 
-/* Per-chain counters since init, to HOST out[8]:
- * [0] algorithmic flop count of the two-site contractions (2 chi_l 3 chi_m 3 chi_r),
+/* Per-chain counters since init, to HOST out[HM_NUM_STATS]:
+ * [0] flops of the two-site contractions, counted block by block
+ *     (2 rows x inner x columns of every charge block, Sec. II.C),
  * [1] gate flops (2 * 81 chi_l chi_r),
- * [2] SVD flops charged at the dense count 4 m^2 n + 8 m n^2 + 9 n^3 (m >= n),
+ * [2] SVD flops of the blocked decompositions: the dense count
+ *     4 M^2 N + 8 M N^2 + 9 N^3 (M >= N) of every charge block,
  * [3] measurement + collapse transfer-matrix flops,
  * [4] sum of discarded weights, [5] largest bond dimension seen,
- * [6] Jacobi sweeps, [7] two-site splits.  Synchronises. */
-int hm_chain_stats(hm_ctx* ctx, hm_chain chain, double* out8);
+ * [6] Jacobi sweeps (largest block of each split; binary32 sweeps under
+ *     HM_MIXED), [7] two-site splits,
+ * [8] the dense-SVD count of the same splits without blocking (what one
+ *     unblocked SVD per split would be charged), [9] binary64 polish sweeps
+ *     (HM_MIXED), [10] charge blocks decomposed, [11] reserved.
+ * Synchronises. */
+int hm_chain_stats(hm_ctx* ctx, hm_chain chain, double* out);
 
 /* Copy the chain's current MPS to the host: dims_out[n_sites + 1] bond dims
  * and the site tensors concatenated into buf (capacity `cap` doubles);

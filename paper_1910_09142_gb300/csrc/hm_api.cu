@@ -226,12 +226,23 @@ std::vector<double> gate_table(const Layout& L) {
   return g;
 }
 
-// Ops plus the gate table they index (entries of gate_table first).
+// Ops plus the gate table they index (entries of gate_table first) and each
+// entry's GI_* bits: GI_EXCHANGE for an odd number of SWAP letters (the two
+// sites' contents change places), GI_MIXING when a bond gate is among the
+// letters (the entry then conserves only m1 + m2, Sec. II.C).
 struct Schedule {
   std::vector<OpDev> ops;
   std::vector<double> gates;          // n_gates * 81
+  std::vector<int32_t> info;          // n_gates
   int32_t n_gates() const { return (int32_t)(gates.size() / 81); }
 };
+
+std::vector<int32_t> gate_info_table(const Layout& L) {
+  std::vector<int32_t> info(GATE_BOND0 + L.bonds.size(), GI_MIXING);
+  info[GATE_ID] = 0;
+  info[GATE_SWAP] = GI_EXCHANGE;
+  return info;
+}
 
 // HM_SCHED_FUSED: one pass over the plain op list with a stack.  A
 // truncating split on the pair (k, k+1) that directly follows another
@@ -293,6 +304,12 @@ void fuse_schedule(Schedule& s) {
         }
         f = entry.emplace(it.word, s.n_gates()).first;
         s.gates.insert(s.gates.end(), P, P + 81);
+        int32_t inf = 0;
+        for (int32_t g : it.word) {
+          if (s.info[g] & GI_EXCHANGE) inf ^= GI_EXCHANGE;
+          inf |= s.info[g] & GI_MIXING;
+        }
+        s.info.push_back(inf);
       }
       it.op.gate = f->second;
     } else {
@@ -304,7 +321,7 @@ void fuse_schedule(Schedule& s) {
 }
 
 Schedule make_schedule(const Layout& L) {
-  Schedule s{plan(L), gate_table(L)};
+  Schedule s{plan(L), gate_table(L), gate_info_table(L)};
   if (L.fused) fuse_schedule(s);
   return s;
 }
@@ -320,7 +337,7 @@ struct MemPlan {
   int32_t sv_cap = 0, chi_cap = 0;
   size_t off_desc, off_ops, off_gates, off_kind, off_mi, off_mj, off_mJ, off_ms, off_reg, off_xb, off_siteptr, off_chi,
       off_env, off_cnt, off_stats, off_status, off_theta, off_W, off_V, off_sig, off_perm, off_envws,
-      off_slots, total;
+      off_ginfo, off_qn, off_sgn, off_meta, off_X, off_slots, total;
 };
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
@@ -346,7 +363,8 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gat
     m.ws_cap = std::max(m.ws_cap, mm * nn);
     m.sv_cap = std::max<int32_t>(m.sv_cap, (int32_t)std::min(mm, nn));
   }
-  m.ws_cap = std::max<int64_t>(m.ws_cap, 2 * (int64_t)m.sv_cap + 2);
+  // theta doubles as the split's value lists (4 sv_cap + 1 doubles)
+  m.ws_cap = std::max<int64_t>(m.ws_cap, 4 * (int64_t)m.sv_cap + 8);
   if (n == 1) m.ws_cap = 64, m.sv_cap = 3;
   // transfer workspace: 10 chi x chi matrices + one right environment per
   // distinct measured end site (measure); the collapse uses the first 7
@@ -365,6 +383,7 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gat
   m.off_desc = take(sizeof(ChainDev));
   m.off_ops = take(std::max<size_t>(n_ops, 1) * sizeof(OpDev));
   m.off_gates = take(81 * sizeof(double) * n_gates);
+  m.off_ginfo = take(n_gates * sizeof(int32_t));
   m.off_kind = take(n * sizeof(int32_t));
   m.off_mi = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
   m.off_mj = take(std::max<size_t>(L.meas.size(), 1) * sizeof(int32_t));
@@ -384,6 +403,11 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gat
   m.off_sig = take(m.sv_cap * sizeof(double));
   m.off_perm = take(m.sv_cap * sizeof(int32_t));
   m.off_envws = take(m.env_cap * sizeof(double));
+  m.off_qn = take((size_t)(n + 1) * m.chi_cap * sizeof(int16_t));
+  m.off_sgn = take(n * sizeof(int32_t));
+  m.off_meta = take(kMetaBytes);
+  // binary32 Jacobi of a charge block too large for shared memory (mixed)
+  m.off_X = p.precision == HM_MIXED ? take(m.ws_cap * sizeof(double)) : 0;
   m.slot_off.resize(n);
   for (int s = 0; s < n; ++s) m.slot_off[s] = take(m.bmax[s] * 3 * m.bmax[s + 1] * sizeof(double));
   m.total = off;
@@ -738,6 +762,11 @@ static int init_chain_impl(hm_ctx* ctx, const hm_params* p, const int8_t* env_in
   d.sig = (double*)(base + mp.off_sig);
   d.perm = (int32_t*)(base + mp.off_perm);
   d.env_ws = (double*)(base + mp.off_envws);
+  d.gate_info = (const int32_t*)(base + mp.off_ginfo);
+  d.qn = (int16_t*)(base + mp.off_qn);
+  d.sgn = (int32_t*)(base + mp.off_sgn);
+  d.meta = base + mp.off_meta;
+  d.X = p->precision == HM_MIXED ? (float*)(base + mp.off_X) : nullptr;
   d.ws_cap = mp.ws_cap;
   d.env_cap = mp.env_cap;
   d.sv_cap = mp.sv_cap;
@@ -745,6 +774,7 @@ static int init_chain_impl(hm_ctx* ctx, const hm_params* p, const int8_t* env_in
   std::memcpy(img.data() + mp.off_desc, &d, sizeof d);
   if (!ch->ops.empty()) std::memcpy(img.data() + mp.off_ops, ch->ops.data(), ch->ops.size() * sizeof(OpDev));
   std::memcpy(img.data() + mp.off_gates, sched.gates.data(), sched.gates.size() * sizeof(double));
+  std::memcpy(img.data() + mp.off_ginfo, sched.info.data(), sched.info.size() * sizeof(int32_t));
   std::memcpy(img.data() + mp.off_kind, L.kind.data(), L.kind.size() * sizeof(int32_t));
   std::vector<int> ends;
   for (size_t q = 0; q < L.meas.size(); ++q) {
@@ -1003,13 +1033,13 @@ int hm_collapse(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, do
   return check_device_error(ctx);
 }
 
-int hm_chain_stats(hm_ctx* ctx, hm_chain chain, double* out8) {
+int hm_chain_stats(hm_ctx* ctx, hm_chain chain, double* out) {
   if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
   auto it = ctx->chains.find(chain);
-  if (it == ctx->chains.end() || !out8) return fail(&ctx->err, HM_ERR_ARG, "unknown chain or null output");
+  if (it == ctx->chains.end() || !out) return fail(&ctx->err, HM_ERR_ARG, "unknown chain or null output");
   HM_CUDA(ctx, cudaSetDevice(ctx->device));
   HM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  HM_CUDA(ctx, cudaMemcpy(out8, ctx->base + it->second->off + it->second->mp.off_stats, ST_N * sizeof(double),
+  HM_CUDA(ctx, cudaMemcpy(out, ctx->base + it->second->off + it->second->mp.off_stats, ST_N * sizeof(double),
                           cudaMemcpyDeviceToHost));
   return check_device_error(ctx);
 }
@@ -1042,6 +1072,27 @@ int hm_get_mps(hm_ctx* ctx, hm_chain chain, int32_t* dims_out, int32_t dims_cap,
     HM_CUDA(ctx, cudaMemcpy(buf + o, base + c->mp.slot_off[s], sz * sizeof(double), cudaMemcpyDeviceToHost));
     o += sz;
   }
+  int32_t cnt[4];
+  HM_CUDA(ctx, cudaMemcpy(cnt, base + c->mp.off_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+  if (cnt[2] == 1) {
+    // the chain stores an S^x-basis sample with every leg rotated by R
+    // (rows: the S^x eigenvectors; R = R^T = R^-1); return it unrotated
+    const double r = 1.0 / std::sqrt(2.0);
+    const double R[9] = {0.5, r, 0.5, r, 0.0, -r, 0.5, -r, 0.5};
+    o = 0;
+    for (int s = 0; s < n; ++s) {
+      const int cl = dims_out[s], cr = dims_out[s + 1];
+      for (int l = 0; l < cl; ++l)
+        for (int x = 0; x < cr; ++x) {
+          double* a = buf + o + (size_t)l * 3 * cr + x;
+          const double a0 = a[0], a1 = a[cr], a2 = a[2 * cr];
+          a[0] = R[0] * a0 + R[1] * a1 + R[2] * a2;
+          a[cr] = R[3] * a0 + R[4] * a1 + R[5] * a2;
+          a[2 * cr] = R[6] * a0 + R[7] * a1 + R[8] * a2;
+        }
+      o += (size_t)cl * 3 * cr;
+    }
+  }
   return check_device_error(ctx);
 }
 
@@ -1070,6 +1121,18 @@ int hm_set_mps(hm_ctx* ctx, hm_chain chain, const int32_t* dims, int32_t n_sites
     HM_CUDA(ctx, cudaMemcpy(base + c->mp.slot_off[s], buf + o, sz * sizeof(double), cudaMemcpyHostToDevice));
     o += sz;
   }
+  // the state is stored as given (frame 0) and carries no charge labels:
+  // the chain evolves in dense mode (one block per split) until its next
+  // collapse resets it to a charge-labelled initial state
+  int32_t cnt[4];
+  HM_CUDA(ctx, cudaMemcpy(cnt, base + c->mp.off_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+  cnt[2] = 0;
+  cnt[3] = 1;
+  HM_CUDA(ctx, cudaMemcpy(base + c->mp.off_cnt, cnt, sizeof cnt, cudaMemcpyHostToDevice));
+  const std::vector<int16_t> q0((size_t)(n + 1) * c->mp.chi_cap, 0);
+  const std::vector<int32_t> s0(n, 0);
+  HM_CUDA(ctx, cudaMemcpy(base + c->mp.off_qn, q0.data(), q0.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  HM_CUDA(ctx, cudaMemcpy(base + c->mp.off_sgn, s0.data(), s0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   c->phase = evolved ? 1 : 0;
   return HM_OK;
 }

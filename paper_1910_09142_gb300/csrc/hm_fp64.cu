@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "hm_block.cuh"
 #include "hm_internal.h"
 
 namespace hm {
@@ -392,8 +393,52 @@ __device__ void two_site_op(ChainDev* c, const OpDev op, int t, Shared& sh, int3
   __syncthreads();
 }
 
+// One two-site op of a chain, block by block in the S^z charge of the new
+// middle bond (Sec. II.C): theta by block GEMMs, the gate within its
+// conserved sectors, a binary64 one-sided Jacobi per block, then one
+// truncation over the union of the blocks' singular values (Sec. II).
+__device__ void two_site_op_blocked(ChainDev* c, const OpDev op, int t, Shared& sh, blk::SplitSh& ss,
+                                    int32_t* ctx_err) {
+  if (!blk::prepare<NT>(c, op, ss)) blk::prepare<NT>(c, op, ss);
+  blk::theta_blocks<NT, TM, TN, TK, double>(c, op.k, ss, c->theta, &sh.g.a[0][0]);
+  const blk::Meta* M = reinterpret_cast<const blk::Meta*>(c->meta);
+  int sweeps = 0;
+  int64_t cost = -1;
+  for (int b = 0; b < ss.nblk; ++b) {
+    const blk::BlockRec& r = M->b[b];
+    double* W = c->W + r.woff;
+    double* V = c->V + r.voff;
+    blk::gather_block<NT, double, double>(c, op.k, ss, r, c->theta, W, r.q, V, r.p);
+    __syncthreads();
+    const int sw = blk::jacobi64<NT>(W, r.q, r.p, V, c->sig, 1e-9, kMaxSweeps, &sh.ival[0], &sh.scal[5]);
+    if (sw < 0) {
+      set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+      return;
+    }
+    const int64_t cb = (int64_t)r.q * r.p * r.p;   // sweeps of the costliest block
+    if (cb > cost) cost = cb, sweeps = sw;
+  }
+  blk::finish<NT>(c, op, t, ss, c->theta, ctx_err, sweeps, 0);
+  if (threadIdx.x == 0 && ss.kk > 0) {
+    double k1 = 0.0;
+    for (int i = 0; i < ss.nin; ++i) {
+      const int Q = M->qin[i];
+      double rows = 0.0, cols = 0.0;
+      for (int u = 0; u < 3; ++u) {
+        rows += blk::seg_of(M, 0, ss.qbase, Q - ss.sk * blk::mval(u)).len;
+        cols += blk::seg_of(M, 2, ss.qbase, Q + ss.sk1 * blk::mval(u)).len;
+      }
+      k1 += 2.0 * rows * blk::seg_of(M, 1, ss.qbase, Q).len * cols;
+    }
+    c->stats[ST_K1] += k1;
+    c->stats[ST_K2] += 2.0 * 81.0 * c->chi[op.k] * c->chi[op.k + 2];
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT) evolve_fp64_kernel(BatchArg b, OutArg o) {
   __shared__ Shared sh;
+  __shared__ blk::SplitSh ss;
   ChainDev* c = b.c[blockIdx.x];
   const OpDev* ops = b.ops_override ? b.ops_override : c->ops;
   const int n_ops = b.ops_override ? b.n_override : c->n_ops;
@@ -401,7 +446,7 @@ __global__ void __launch_bounds__(NT) evolve_fp64_kernel(BatchArg b, OutArg o) {
   for (int t = b.t0; t < t1; ++t) {
     if (*(volatile int32_t*)c->status != 0) return;
     __syncthreads();
-    two_site_op(c, ops[t], t, sh, o.ctx_err);
+    two_site_op_blocked(c, ops[t], t, sh, ss, o.ctx_err);
     __syncthreads();
   }
 }
@@ -434,6 +479,13 @@ __device__ __constant__ double kSz[9] = {1, 0, 0, 0, 0, 0, 0, 0, -1};
 // S+ = sqrt(2) (|+1><0| + |0><-1|); S- its transpose (basis m = +1, 0, -1)
 __device__ __constant__ double kSp[9] = {0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0, 0, 0};
 __device__ __constant__ double kSm[9] = {0, 0, 0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0};
+// S^x = (S+ + S-)/2 and A = (S+ - S-)/2 = i S^y, so S^y_i S^y_j = -A_i A_j.
+__device__ __constant__ double kSx[9] = {0, 0.7071067811865476, 0, 0.7071067811865476, 0, 0.7071067811865476,
+                                         0, 0.7071067811865476, 0};
+__device__ __constant__ double kAy[9] = {0, 0.7071067811865476, 0, -0.7071067811865476, 0, 0.7071067811865476,
+                                         0, -0.7071067811865476, 0};
+__device__ __constant__ double kAyNeg[9] = {0, -0.7071067811865476, 0, 0.7071067811865476, 0, -0.7071067811865476,
+                                            0, 0.7071067811865476, 0};
 
 // Right environment through one site: Rout[i, j] = sum_s A^s Rin A^{sT}
 // (Rin cr x cr, Rout cl x cl).  Y: 3cl x cr scratch.
@@ -496,8 +548,13 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
   __syncthreads();
   int pos = 0, cur = 0;
   double E_est = 0.0;
-  const double* ops1[3] = {kSz, kSp, kSm};
-  const double* ops2[3] = {kSz, kSm, kSp};
+  // A chain in frame 1 stores R^N |psi> (R exchanges S^x and S^z, R S^z R =
+  // S^x): there <Sz_i Sz_j> of |psi> is <Sx_i Sx_j> of the stored state, and
+  // S_i.S_j is invariant.  Frame 0: (Sz Sz, S+ S-, S- S+); frame 1:
+  // (Sx Sx, Sz Sz, A (-A)), whose sum is S.S.
+  const int frame = c->counters[2];
+  const double* ops1[3] = {frame ? kSx : kSz, frame ? kSz : kSp, frame ? kAy : kSm};
+  const double* ops2[3] = {frame ? kSx : kSz, frame ? kSz : kSm, frame ? kAyNeg : kSp};
   int bi = 0;
   while (bi < c->n_meas) {
     const int a = c->meas_i[bi];
@@ -530,7 +587,8 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
     if (tid == 0) {
       for (int q = bi; q < bend; ++q) {
         const double zz = vals[0][q - bi] / nrm;
-        const double ss = zz + 0.5 * (vals[1][q - bi] + vals[2][q - bi]) / nrm;
+        const double ss = frame ? zz + (vals[1][q - bi] + vals[2][q - bi]) / nrm
+                                : zz + 0.5 * (vals[1][q - bi] + vals[2][q - bi]) / nrm;
         out[1 + 2 * q] = ss;
         out[2 + 2 * q] = zz;
         E_est += c->meas_J[q] * ss;
@@ -759,8 +817,11 @@ __global__ void __launch_bounds__(NT) collapse_fp64_kernel(BatchArg b, OutArg o)
   if (*(volatile int32_t*)c->status != 0) return;
   const int n_sample = c->counters[0];
   const int basis = (c->basis_zx && (n_sample & 1)) ? 1 : 0;
+  // the measured basis as seen by the stored state: R maps the S^z basis to
+  // the S^x basis and back (R e_b = v_b, R v_b = e_b), so a frame-1 state is
+  // measured in the other basis; the outcome order is the same
   double B[9];
-  basis_rows(c, basis, B);
+  basis_rows(c, basis ^ c->counters[2], B);
   const int64_t cc = (int64_t)c->chi_cap * c->chi_cap;
   double* R[2] = {c->env_ws, c->env_ws + cc};
   double* X = c->env_ws + 2 * cc;      // cl x 3cr
@@ -879,9 +940,16 @@ __global__ void __launch_bounds__(NT) collapse_fp64_kernel(BatchArg b, OutArg o)
 
 // Writes the initial state |i>_E |B>_C from env_out and counters[1]
 // (Sec. I.C.1 step 1): environment sites (1,3,1) basis vectors, cluster
-// physical sites delta(s,a)/sqrt(3) of shape (1,3,3), ancillas delta(a,s) of
-// shape (3,3,1).  With draw_initial, first draws the environment in the Sz
-// basis with p = 1/3 each and sample index n = -1.
+// physical sites delta(s, 2 - a)/sqrt(3) of shape (1,3,3), ancillas
+// delta(2 - a, s) of shape (3,3,1) (the Bell bond ordered by ascending
+// S^z charge).  An environment drawn in the S^x basis is stored in frame 1:
+// every leg rotated by R (rows: the S^x eigenvectors), which maps the S^x
+// eigenvector v_b to e_b and leaves the Bell pairs and the Heisenberg gates
+// unchanged (R is real orthogonal and the gates commute with R (x) R), so
+// every initial state is a product of S^z eigenstates and Bell pairs with
+// definite total S^z, and every sample evolves in charge blocks (Sec. II.C).
+// With draw_initial, first draws the environment in the Sz basis with
+// p = 1/3 each and sample index n = -1.
 __global__ void __launch_bounds__(NT) reset_kernel(BatchArg b, OutArg o, int draw_initial) {
   ChainDev* c = b.c[blockIdx.x];
   const int tid = threadIdx.x;
@@ -899,9 +967,6 @@ __global__ void __launch_bounds__(NT) reset_kernel(BatchArg b, OutArg o, int dra
     }
     __syncthreads();
   }
-  const int basis = c->counters[1];
-  double B[9];
-  basis_rows(c, basis, B);
   const double r3 = 1.0 / sqrt(3.0);
   // env ordinal of site k = number of env sites before k
   for (int k = tid; k < c->n_sites; k += NT) {
@@ -911,15 +976,41 @@ __global__ void __launch_bounds__(NT) reset_kernel(BatchArg b, OutArg o, int dra
       int ord = 0;
       for (int s = 0; s < k; ++s) ord += c->site_kind[s] == SITE_ENV;
       const int pick = c->env_out[ord];
-      for (int s = 0; s < 3; ++s) A[s] = B[3 * pick + s];
+      for (int s = 0; s < 3; ++s) A[s] = s == pick ? 1.0 : 0.0;
+      c->sgn[k] = 1;
     } else if (kind == SITE_CPHYS) {
-      for (int e = 0; e < 9; ++e) A[e] = (e % 4 == 0) ? r3 : 0.0;
+      for (int e = 0; e < 9; ++e) A[e] = (e / 3 == 2 - e % 3) ? r3 : 0.0;     // A[0, s, a]
+      c->sgn[k] = 1;
     } else {
-      for (int e = 0; e < 9; ++e) A[e] = (e % 4 == 0) ? 1.0 : 0.0;
+      for (int e = 0; e < 9; ++e) A[e] = (e / 3 == 2 - e % 3) ? 1.0 : 0.0;    // A[a, s, 0]
+      c->sgn[k] = -1;
     }
   }
   for (int i = tid; i <= c->n_sites; i += NT)
     c->chi[i] = (i > 0 && i < c->n_sites && c->site_kind[i - 1] == SITE_CPHYS) ? 3 : 1;
+  if (tid == 0) {
+    // bond charges: q_0 = 0, q_{k+1} = q_k + m(pick) after an environment
+    // site; the Bell bond carries q_k + (-1, 0, +1); back to q_k after the ancilla
+    const int cap = c->chi_cap;
+    int q = 0, ord = 0;
+    c->qn[0] = 0;
+    for (int k = 0; k < c->n_sites; ++k) {
+      const int kind = c->site_kind[k];
+      int16_t* next = c->qn + (size_t)(k + 1) * cap;
+      if (kind == SITE_ENV) {
+        q += 1 - c->env_out[ord++];
+        next[0] = (int16_t)q;
+      } else if (kind == SITE_CPHYS) {
+        next[0] = (int16_t)(q - 1);
+        next[1] = (int16_t)q;
+        next[2] = (int16_t)(q + 1);
+      } else {
+        next[0] = (int16_t)q;
+      }
+    }
+    c->counters[2] = c->counters[1];
+    c->counters[3] = 0;
+  }
 }
 
 }  // namespace

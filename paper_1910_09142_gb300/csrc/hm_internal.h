@@ -24,7 +24,17 @@ struct OpDev {
 };
 
 // Per-chain statistics slots (doubles), see hm_chain_stats.
-enum : int { ST_K1 = 0, ST_K2, ST_SVD, ST_TRANSFER, ST_DISC, ST_MAXCHI, ST_SWEEPS, ST_SPLITS, ST_N };
+enum : int {
+  ST_K1 = 0, ST_K2, ST_SVD, ST_TRANSFER, ST_DISC, ST_MAXCHI, ST_SWEEPS, ST_SPLITS,
+  ST_SVD_DENSE, ST_SWEEPS64, ST_BLOCKS, ST_RESERVED, ST_N
+};
+static_assert(ST_N == HM_NUM_STATS, "statistics slots of the C ABI");
+
+// Bits of a gate table entry's info word (ChainDev::gate_info).
+enum : int32_t {
+  GI_EXCHANGE = 1,   // moves the two sites' contents across (an odd number of SWAP letters)
+  GI_MIXING = 2      // not a permutation: conserves m1 + m2 only (a bond gate or a product with one)
+};
 
 // Device-resident description and state of one chain.  Lives in the arena;
 // every pointer is a device address inside the same chain block.
@@ -44,11 +54,14 @@ struct ChainDev {
   const int32_t* region;     // n_region physical sites of the measured columns (sorted)
   int32_t n_region, pad1;
   const double* xbasis;      // 9: rows are the Sx eigenvectors (m=+1,0,-1 order)
+  const int32_t* gate_info;  // n_gates: GI_* bits
   // mutable state
   double** site;             // n_sites device pointers (fixed slots)
   int32_t* chi;              // n_sites + 1 bond dims; site s is (chi[s], 3, chi[s+1])
   int32_t* env_out;          // n_env: basis index of the current environment state
-  int32_t* counters;         // [0] sample index n, [1] basis of the current initial state
+  int32_t* counters;         // [0] sample index n, [1] basis of the current initial state,
+                             // [2] frame of the stored state (0: as is, 1: every leg rotated by R,
+                             //     which exchanges S^x and S^z), [3] dense mode (no charge labels)
   double* stats;             // ST_N
   int32_t* status;           // 0 = ok, else a negative HM_ERR_* code
   int32_t* err_where;        // op index / site where the error happened
@@ -59,9 +72,15 @@ struct ChainDev {
   double* sig;               // sv_cap: sorted singular values
   int32_t* perm;             // sv_cap: sorted index -> Jacobi column
   double* env_ws;            // env_cap: transfer-matrix workspace (measure, collapse)
+  int16_t* qn;               // (n_sites + 1) x chi_cap: S^z charge of every bond index (grouped, ascending)
+  int32_t* sgn;              // n_sites: charge sign of each position's leg (+1 spin, -1 ancilla, 0 dense)
+  void* meta;                // split metadata (charge runs, blocks), kMetaBytes
+  float* X;                  // ws_cap doubles of binary32 scratch (mixed chains), or nullptr
   int64_t ws_cap, env_cap;
   int32_t sv_cap, chi_cap;
 };
+
+constexpr size_t kMetaBytes = 80 * 1024;   // >= sizeof(blk::Meta) (checked in hm_block.cuh)
 
 constexpr int kMaxBatch = 448;   // chains per launch (kernel parameter block < 4 KB)
 

@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <mutex>
 
+#include "hm_block.cuh"
 #include "hm_internal.h"
 
 namespace hm {
@@ -39,65 +40,6 @@ __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-__device__ __forceinline__ double warp_sumd(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// C (M x N, row-major binary32) = A (M x K, row-major binary64) * B (K x N,
-// row-major binary64), operands rounded to binary32 on load.
-__device__ void cta_gemm_f32(int M, int N, int K, const double* __restrict__ A, int lda,
-                             const double* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
-                             float* sm) {
-  float* sa = sm;               // [GK][GM]
-  float* sb = sm + GK * GM;     // [GK][GN]
-  const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;   // 16 x 32 threads: rows ty + 32 r (r < 2), cols tx + 16 c (c < 4)
-  for (int i0 = 0; i0 < M; i0 += GM) {
-    for (int j0 = 0; j0 < N; j0 += GN) {
-      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-      for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int e = tid; e < GM * GK; e += NT) {
-          const int kk = e % GK, ii = e / GK;
-          const int gi = i0 + ii, gk = k0 + kk;
-          sa[kk * GM + ii] = (gi < M && gk < K) ? (float)A[(size_t)gi * lda + gk] : 0.f;
-        }
-        for (int e = tid; e < GN * GK; e += NT) {
-          const int jj = e % GN, kk = e / GN;
-          const int gj = j0 + jj, gk = k0 + kk;
-          sb[kk * GN + jj] = (gj < N && gk < K) ? (float)B[(size_t)gk * ldb + gj] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-          float a[2], b[4];
-#pragma unroll
-          for (int r = 0; r < 2; ++r) a[r] = sa[kk * GM + ty + 32 * r];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) b[c] = sb[kk * GN + tx + 16 * c];
-#pragma unroll
-          for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-        }
-        __syncthreads();
-      }
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int i = i0 + ty + 32 * r;
-        if (i >= M) continue;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int j = j0 + tx + 16 * c;
-          if (j < N) C[(size_t)i * ldc + j] = acc[r][c];
-        }
-      }
-    }
-  }
-  __syncthreads();
 }
 
 // Rotate the column pair (x, y) of length q (W) and (vx, vy) of length p (V)
@@ -277,7 +219,7 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
   const int nb = (p + b - 1) / b;
   int done = 0;
   bool converged = false;
-  {
+  if (tmp) {
     // order the columns by decreasing norm before the first sweep (W and V
     // permuted together, so W = X V still holds): the graded two-site
     // matrices converge in ~1 sweep fewer (12.3 -> 11.3 for 256 < p <= 512)
@@ -378,6 +320,88 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
   return converged ? done : -1;
 }
 
+// One-sided Jacobi in binary32 on a charge block held entirely in shared
+// memory: W (q x p column-major, leading dimension ldw), V (p x p, leading
+// dimension ldv, holds the starting basis), column norms cached in nrm and
+// recomputed at every sweep start.  Round-robin pairing, one warp per pair.
+// Same stopping rule as cta_jacobi_f32.  Returns the sweeps, or -1.
+__device__ int jacobi32_smem(float* W, int q, int ldw, int p, float* V, int ldv, float* nrm, Scal& sc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarps = NT / 32;
+  const float tol = sqrtf((float)q) * FLT_EPSILON;
+  const int p2 = p + (p & 1);
+  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    for (int j = warp; j < p; j += nwarps) {
+      const float* cj = W + (size_t)j * ldw;
+      float s2 = 0.f;
+      for (int i = lane; i < q; i += 32) s2 = fmaf(cj[i], cj[i], s2);
+      s2 = warp_sumf(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
+    if (tid == 0) {
+      sc.ival[0] = 0;
+      sc.ival[2] = 0;
+    }
+    __syncthreads();
+    int rot = 0;
+    float rmax = 0.f;
+    for (int rd = 0; rd < p2 - 1; ++rd) {
+      for (int pi = warp; pi < p2 / 2; pi += nwarps) {
+        int a, b;
+        if (pi == 0) {
+          a = rd;
+          b = p2 - 1;
+        } else {
+          a = (rd + pi) % (p2 - 1);
+          b = (rd - pi + (p2 - 1)) % (p2 - 1);
+        }
+        if (a >= p || b >= p) continue;
+        float* x = W + (size_t)a * ldw;
+        float* y = W + (size_t)b * ldw;
+        float ga = 0.f;
+        for (int i = lane; i < q; i += 32) ga = fmaf(x[i], y[i], ga);
+        ga = warp_sumf(ga);
+        const float al = nrm[a], be = nrm[b];
+        if (ga != 0.f && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+          rmax = fmaxf(rmax, fabsf(ga) / (sqrtf(al) * sqrtf(be)));
+          const float zeta = (be - al) / (2.f * ga);
+          float t;
+          if (fabsf(zeta) > 1e18f) t = 0.5f / zeta;
+          else t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+          for (int i = lane; i < q; i += 32) {
+            const float u = x[i], v = y[i];
+            x[i] = cs * u - sn * v;
+            y[i] = sn * u + cs * v;
+          }
+          float* vx = V + (size_t)a * ldv;
+          float* vy = V + (size_t)b * ldv;
+          for (int i = lane; i < p; i += 32) {
+            const float u = vx[i], v = vy[i];
+            vx[i] = cs * u - sn * v;
+            vy[i] = sn * u + cs * v;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            nrm[a] = al - t * ga;
+            nrm[b] = be + t * ga;
+          }
+          rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (rot && lane == 0) sc.ival[0] = 1;
+    if (lane == 0) atomicMax(&sc.ival[2], __float_as_int(rmax));
+    __syncthreads();
+    const int any = sc.ival[0];
+    const float rm = __int_as_float(sc.ival[2]);
+    __syncthreads();
+    if (!any || rm < 2e-4f) return sweep;
+  }
+  return -1;
+}
+
 __device__ void set_error(const ChainDev* c, int code, int where, int32_t* ctx_err) {
   if (threadIdx.x == 0) {
     if (atomicCAS(c->status, 0, code) == 0) *c->err_where = where;
@@ -385,165 +409,94 @@ __device__ void set_error(const ChainDev* c, int code, int where, int32_t* ctx_e
   }
 }
 
-__device__ int truncation_rank(const double* s, int n, int chi_max, double cutoff, double* tail, double* total_out) {
-  tail[n] = 0.0;
-  for (int q = n - 1; q >= 0; --q) tail[q] = tail[q + 1] + s[q] * s[q];
-  const double total = tail[0];
-  *total_out = total;
-  int k = n;
-  for (int kk = 1; kk <= n; ++kk) {
-    if (tail[kk] <= cutoff * total) {
-      k = kk;
-      break;
-    }
-  }
-  if (k > chi_max) k = chi_max;
-  while (k > 1 && k < n && s[k] >= s[k - 1] * (1.0 - 1e-8)) --k;
-  return k;
-}
+// Shared memory of the binary32 block Jacobi; the kernel's dynamic shared
+// memory is at least this (and at least the staged fallback's plan).
+constexpr size_t kBlockSmem = 210 * 1024;
 
+// Stopping rule of the binary64 polish: a sweep whose largest rotation ratio
+// is below this leaves off-diagonals of order its square for the next sweep.
+constexpr double kPolishStop = 1e-7;
+
+// One two-site op (step 2 of Sec. I.C.1) in charge blocks (Sec. II.C):
+// theta and the gate in binary32 (operands rounded from the binary64 site
+// tensors, binary32 accumulation); per block a binary32 one-sided Jacobi in
+// shared memory (global memory with staged column blocks when the block does
+// not fit) as a preconditioner, then binary64 sweeps on the promoted W and V
+// until the binary64 stopping rule holds, so the singular values and the
+// kept vectors are binary64-accurate for that theta; then the truncation
+// rule (Sec. II), renormalisation and absorb in binary64.
 __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols, float* smem, Scal& sc,
-                                  int32_t* ctx_err) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k = op.k;
-  const int chil = c->chi[k], chim = c->chi[k + 1], chir = c->chi[k + 2];
-  const int m = 3 * chil, n = 3 * chir;
-  double* Ak = c->site[k];
-  double* Ak1 = c->site[k + 1];
+                                  blk::SplitSh& ss, int32_t* ctx_err) {
+  if (!blk::prepare<NT>(c, op, ss)) blk::prepare<NT>(c, op, ss);
   float* theta = reinterpret_cast<float*>(c->theta);
-  float* W = reinterpret_cast<float*>(c->W);
-  float* V = reinterpret_cast<float*>(c->V);
-
-  cta_gemm_f32(m, n, chim, Ak, chim, Ak1, n, theta, n, smem);
-
-  const bool trans = n > m;
-  const int q = trans ? n : m, p = trans ? m : n;
-  const double* Gd = c->gates + (size_t)op.gate * 81;
-  float* G = smem;
-  for (int e = tid; e < 81; e += NT) G[e] = (float)Gd[e];
-  __syncthreads();
-  for (int e = tid; e < chil * chir; e += NT) {
-    const int l = e / chir, r = e % chir;
-    float th[9];
-#pragma unroll
-    for (int s1 = 0; s1 < 3; ++s1)
-#pragma unroll
-      for (int s2 = 0; s2 < 3; ++s2) th[3 * s1 + s2] = theta[(size_t)(3 * l + s1) * n + s2 * chir + r];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        float x = 0.f;
-#pragma unroll
-        for (int u = 0; u < 9; ++u) x = fmaf(G[(3 * a + b) * 9 + u], th[u], x);
-        const int row = 3 * l + a, col = b * chir + r;
-        if (!trans) W[(size_t)col * q + row] = x;
-        else W[(size_t)row * q + col] = x;
+  blk::theta_blocks<NT, GM, GN, GK, float>(c, op.k, ss, theta, smem);
+  const blk::Meta* M = reinterpret_cast<const blk::Meta*>(c->meta);
+  int sw32 = 0, sw64 = 0;
+  int64_t cost = -1;
+  for (int b = 0; b < ss.nblk; ++b) {
+    const blk::BlockRec& r = M->b[b];
+    const int q = r.q, p = r.p;
+    const int ldw = q | 1, ldv = p | 1;         // odd strides: conflict-free column walks
+    const size_t need = ((size_t)p * ldw + (size_t)p * ldv + (size_t)p) * sizeof(float);
+    float* W32;
+    float* V32;
+    int lw, lv, sw;
+    if (need <= kBlockSmem) {
+      W32 = smem;
+      V32 = smem + (size_t)p * ldw;
+      blk::gather_block<NT, float, float>(c, op.k, ss, r, theta, W32, ldw, V32, ldv);
+      __syncthreads();
+      sw = jacobi32_smem(W32, q, ldw, p, V32, ldv, V32 + (size_t)p * ldv, sc);
+      lw = ldw;
+      lv = ldv;
+    } else {
+      W32 = c->X;
+      V32 = c->X + (size_t)q * p;
+      blk::gather_block<NT, float, float>(c, op.k, ss, r, theta, W32, q, V32, p);
+      __syncthreads();
+      sw = cta_jacobi_f32(W32, q, p, V32, bcols, smem, sc, nullptr);
+      lw = q;
+      lv = p;
+    }
+    if (sw < 0) {
+      set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+      return;
+    }
+    double* W64 = c->W + r.woff;
+    double* V64 = c->V + r.voff;
+    for (int e = threadIdx.x; e < q * p; e += NT) W64[e] = (double)W32[(size_t)(e / q) * lw + e % q];
+    for (int e = threadIdx.x; e < p * p; e += NT) V64[e] = (double)V32[(size_t)(e / p) * lv + e % p];
+    __syncthreads();
+    const int s64 = blk::jacobi64<NT>(W64, q, p, V64, c->sig, kPolishStop, kMaxSweeps, &sc.ival[0], &sc.dval[1]);
+    if (s64 < 0) {
+      set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+      return;
+    }
+    const int64_t cb = (int64_t)q * p * p;
+    if (cb > cost) cost = cb, sw32 = sw, sw64 = s64;
+  }
+  blk::finish<NT>(c, op, t, ss, c->theta, ctx_err, sw32, sw64);
+  if (threadIdx.x == 0 && ss.kk > 0) {
+    double k1 = 0.0;
+    for (int i = 0; i < ss.nin; ++i) {
+      const int Q = M->qin[i];
+      double rows = 0.0, cols = 0.0;
+      for (int u = 0; u < 3; ++u) {
+        rows += blk::seg_of(M, 0, ss.qbase, Q - ss.sk * blk::mval(u)).len;
+        cols += blk::seg_of(M, 2, ss.qbase, Q + ss.sk1 * blk::mval(u)).len;
       }
-  }
-  __syncthreads();
-
-  const int sweeps = cta_jacobi_f32(W, q, p, V, bcols, smem, sc, theta);   // theta is free here
-  if (sweeps < 0) {
-    set_error(c, HM_ERR_NUMERIC, t, ctx_err);
-    return;
-  }
-  // singular values (norms accumulated in binary64), rank sort, truncation
-  double* sig_raw = c->theta;       // theta is free now (binary64 view)
-  double* tail = c->theta + p;
-  for (int j = warp; j < p; j += NT / 32) {
-    const float* cj = W + (size_t)j * q;
-    double s2 = 0.0;
-    for (int i = lane; i < q; i += 32) s2 = fma((double)cj[i], (double)cj[i], s2);
-    s2 = warp_sumd(s2);
-    if (lane == 0) sig_raw[j] = sqrt(s2);
-  }
-  __syncthreads();
-  for (int j = tid; j < p; j += NT) {
-    const double sj = sig_raw[j];
-    int rank = 0;
-    for (int i = 0; i < p; ++i) {
-      const double si = sig_raw[i];
-      rank += (si > sj) || (si == sj && i < j);
+      k1 += 2.0 * rows * blk::seg_of(M, 1, ss.qbase, Q).len * cols;
     }
-    c->sig[rank] = sj;
-    c->perm[rank] = j;
+    c->stats[ST_K1] += k1;
+    c->stats[ST_K2] += 2.0 * 81.0 * c->chi[op.k] * c->chi[op.k + 2];
   }
-  __syncthreads();
-  if (tid == 0) {
-    const double* s = c->sig;
-    double total, nrm = 1.0;
-    int kk;
-    if (!op.exact) {
-      kk = truncation_rank(s, p, c->chi_max, c->cutoff, tail, &total);
-      if (!(total > 0.0) || !isfinite(total)) kk = -1;
-      else {
-        double kept = 0.0;
-        for (int i = 0; i < kk; ++i) kept += s[i] * s[i];
-        nrm = 1.0 / sqrt(kept);
-        c->stats[ST_DISC] += tail[kk] / total;
-      }
-    } else {
-      kk = 0;
-      while (kk < p && kk < chim && s[kk] > 0.0) ++kk;
-      if (kk == 0) kk = -1;
-    }
-    sc.ival[1] = kk;
-    sc.dval[0] = nrm;
-    if (kk > 0) {
-      const double mm = (double)(m > n ? m : n), nn = (double)(m > n ? n : m);
-      c->stats[ST_K1] += 2.0 * chil * 3.0 * chim * 3.0 * chir;
-      c->stats[ST_K2] += 2.0 * 81.0 * chil * chir;
-      c->stats[ST_SVD] += 4.0 * mm * mm * nn + 8.0 * mm * nn * nn + 9.0 * nn * nn * nn;
-      c->stats[ST_SWEEPS] += sweeps;
-      c->stats[ST_SPLITS] += 1.0;
-      if (kk > c->stats[ST_MAXCHI]) c->stats[ST_MAXCHI] = kk;
-    }
-  }
-  __syncthreads();
-  const int kk = sc.ival[1];
-  const double nrm = sc.dval[0];
-  if (kk <= 0) {
-    set_error(c, HM_ERR_NUMERIC, t, ctx_err);
-    return;
-  }
-  const bool absorb_left = op.absorb == 0;
-  for (int e = tid; e < m * kk; e += NT) {
-    const int row = e / kk, i = e % kk;
-    const int j = c->perm[i];
-    const double sg = c->sig[i];
-    double v;
-    if (!trans) {
-      const double w = W[(size_t)j * q + row];
-      v = absorb_left ? w * nrm : w / sg;
-    } else {
-      const double u = V[(size_t)j * p + row];
-      v = absorb_left ? u * sg * nrm : u;
-    }
-    Ak[e] = v;
-  }
-  for (int e = tid; e < kk * n; e += NT) {
-    const int i = e / n, col = e % n;
-    const int j = c->perm[i];
-    const double sg = c->sig[i];
-    double v;
-    if (!trans) {
-      const double u = V[(size_t)j * p + col];
-      v = absorb_left ? u : u * sg * nrm;
-    } else {
-      const double w = W[(size_t)j * q + col];
-      v = absorb_left ? w / sg : w * nrm;
-    }
-    Ak1[e] = v;
-  }
-  __syncthreads();
-  if (tid == 0) c->chi[k + 1] = kk;
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, int bcols) {
   extern __shared__ float smem[];
   __shared__ Scal sc;
+  __shared__ blk::SplitSh ss;
   ChainDev* c = b.c[blockIdx.x];
   const OpDev* ops = b.ops_override ? b.ops_override : c->ops;
   const int n_ops = b.ops_override ? b.n_override : c->n_ops;
@@ -551,7 +504,7 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
   for (int t = b.t0; t < t1; ++t) {
     if (*(volatile int32_t*)c->status != 0) return;
     __syncthreads();
-    two_site_op_mixed(c, ops[t], t, bcols, smem, sc, o.ctx_err);
+    two_site_op_mixed(c, ops[t], t, bcols, smem, sc, ss, o.ctx_err);
     __syncthreads();
   }
 }
@@ -561,7 +514,8 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
 int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* stream) {
   if (b.n <= 0) return HM_OK;
   int bcols = 16;
-  const size_t smem = mixed_smem_bytes(chi_cap, &bcols);
+  const size_t plan = mixed_smem_bytes(chi_cap, &bcols);
+  const size_t smem = plan > kBlockSmem ? plan : kBlockSmem;
   // the shared-memory opt-in is per device: cache it per device ordinal,
   // under a lock (serving workers may launch from several host threads)
   static std::mutex mu;

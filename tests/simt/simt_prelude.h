@@ -90,6 +90,13 @@ inline int atomicMax(int* p, int value) {
   }
   return old;
 }
+inline int atomicMin(int* p, int value) {
+  std::atomic_ref<int> r(*p);
+  int old = r.load();
+  while (old > value && !r.compare_exchange_weak(old, value)) {
+  }
+  return old;
+}
 inline unsigned long long atomicMax(unsigned long long* p, unsigned long long value) {
   std::atomic_ref<unsigned long long> r(*p);
   unsigned long long old = r.load();
