@@ -25,6 +25,7 @@ HM_ZX_ALTERNATE = 0
 HM_Z_ONLY = 1
 HM_SCHED_PLAIN = 0
 HM_SCHED_FUSED = 1
+HM_NUM_STATS = 12
 SCHEDULES = {"plain": HM_SCHED_PLAIN, "fused": HM_SCHED_FUSED}
 
 _ERRNAMES = {HM_ERR_ARG: "HM_ERR_ARG", HM_ERR_NOMEM: "HM_ERR_NOMEM", HM_ERR_CUDA: "HM_ERR_CUDA",
@@ -300,7 +301,7 @@ class Context:
         self._c(self.lib.hm_collapse_device(self.h, ptr, len(arr), e, lp))
 
     def stats(self, cid):
-        out = np.zeros(8)
+        out = np.zeros(HM_NUM_STATS)
         self._c(self.lib.hm_chain_stats(self.h, cid, _ptr(out)))
         return out
 

@@ -349,21 +349,186 @@ __device__ void gather_block(const ChainDev* c, int k, const SplitSh& s, const B
     const int l = r.rst[a] + v - r.roff[a];
     const int rr = r.cst[b] + u - r.coff[b];
     const int msk = s.mask[3 * a + b];
-    TT x = TT(0);
+    TT x = TT(0), y = TT(0);
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
       if (msk & (1 << t)) {
         const int s1 = t / 3, s2 = t % 3;
-        x += (TT)s.G[(3 * a + b) * 9 + t] * theta[(size_t)(3 * l + s1) * n + s2 * chir + rr];
+        const TT th = theta[(size_t)(3 * l + s1) * n + s2 * chir + rr];
+        const double g = s.G[(3 * a + b) * 9 + t];
+        const TT ghi = (TT)g;
+        x = fma(ghi, th, x);
+        // a binary32 theta takes each coefficient as a binary32 pair
+        // (hi + lo): rounding the gate itself would repeat the same relative
+        // error at every application of that gate and add up coherently over
+        // the evolution, while the rounding of the products does not
+        if (sizeof(TT) < sizeof(double)) y = fma((TT)(g - (double)ghi), th, y);
       }
     }
-    if (r.trans) W[(size_t)v * ldw + u] = (TW)x;
-    else W[(size_t)u * ldw + v] = (TW)x;
+    if (r.trans) W[(size_t)v * ldw + u] = (TW)(x + y);
+    else W[(size_t)u * ldw + v] = (TW)(x + y);
   }
   for (int e = threadIdx.x; e < r.p * r.p; e += NT) {
     const int j = e / r.p, i = e % r.p;
     V[(size_t)j * ldv + i] = (i == j) ? TW(1) : TW(0);
   }
+}
+
+// Barrier of the nthreads threads (a multiple of 32) of a warp group; ids
+// 1..15 (0 is __syncthreads).  HM_HOST_EMULATION: the kernels compiled as
+// host C++ by the CPU emulation of the tests.
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+#if defined(__CUDA_ARCH__)
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+#elif defined(HM_HOST_EMULATION)
+  simt::named_sync(id, nthreads);
+#endif
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-group convergence words of a grouped Jacobi (shared memory).
+struct GroupSh {
+  int32_t flag[16];
+  uint32_t rbits[16];                     // largest rotation ratio of the sweep, binary32 bits
+};
+
+// One-sided (Hestenes) Jacobi run by a group of nw warps (warp lw of the
+// group, barrier id bar): W (q x p column-major, q >= p, leading dimension
+// ldw), rotations accumulated into V (p x p, leading dimension ldv, holds the
+// starting basis), column norms cached in nrm and recomputed at every sweep
+// start.  Round-robin pairing (every round's pairs are disjoint), one warp
+// per pair.  Stops after a sweep with no rotation or whose largest ratio
+// |g| / sqrt(a b) is below `stop` (the next sweep's off-diagonals are then of
+// order stop^2).  Several groups run different charge blocks at once, so a
+// split's blocks share the CTA instead of taking turns.  Returns the sweeps,
+// or -1 when max_sweeps ran out.
+template <typename T>
+__device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, T* __restrict__ V, int ldv,
+                            T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
+  const int lane = threadIdx.x & 31;
+  const int nthr = 32 * nw;
+  const T eps = sizeof(T) == sizeof(double) ? T(2.220446049250313e-16) : T(1.1920928955078125e-07);
+  const T tol = sqrt((T)q) * eps;
+  const T huge = sizeof(T) == sizeof(double) ? T(1e150) : T(1e18);
+  const int p2 = p + (p & 1);
+  for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
+    for (int j = lw; j < p; j += nw) {
+      const T* cj = W + (size_t)j * ldw;
+      T s2 = T(0);
+      for (int i = lane; i < q; i += 32) s2 = fma(cj[i], cj[i], s2);
+      s2 = warp_sum_t(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
+    if (lw == 0 && lane == 0) {
+      gs.flag[g] = 0;
+      gs.rbits[g] = 0u;
+    }
+    group_sync(bar, nthr);
+    T rmax = T(0);
+    int rot = 0;
+    for (int rd = 0; rd < p2 - 1; ++rd) {
+      for (int pi = lw; pi < p2 / 2; pi += nw) {
+        int a, b;
+        if (pi == 0) {
+          a = rd;
+          b = p2 - 1;
+        } else {
+          a = (rd + pi) % (p2 - 1);
+          b = (rd - pi + (p2 - 1)) % (p2 - 1);
+        }
+        if (a >= p || b >= p) continue;
+        T* x = W + (size_t)a * ldw;
+        T* y = W + (size_t)b * ldw;
+        T ga = T(0);
+        for (int i = lane; i < q; i += 32) ga = fma(x[i], y[i], ga);
+        ga = warp_sum_t(ga);
+        const T al = nrm[a], be = nrm[b];
+        if (ga != T(0) && al > T(0) && be > T(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          rmax = fmax(rmax, fabs(ga) / (sqrt(al) * sqrt(be)));
+          const T zeta = (be - al) / (T(2) * ga);
+          T t;
+          if (fabs(zeta) > huge) t = T(0.5) / zeta;
+          else t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+          for (int i = lane; i < q; i += 32) {
+            const T u = x[i], v = y[i];
+            x[i] = cs * u - sn * v;
+            y[i] = sn * u + cs * v;
+          }
+          T* vx = V + (size_t)a * ldv;
+          T* vy = V + (size_t)b * ldv;
+          for (int i = lane; i < p; i += 32) {
+            const T u = vx[i], v = vy[i];
+            vx[i] = cs * u - sn * v;
+            vy[i] = sn * u + cs * v;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            nrm[a] = al - t * ga;
+            nrm[b] = be + t * ga;
+          }
+          rot = 1;
+        }
+      }
+      group_sync(bar, nthr);
+    }
+    if (lane == 0) {
+      if (rot) atomicMax(&gs.flag[g], 1);
+      atomicMax(&gs.rbits[g], __float_as_uint((float)rmax));
+    }
+    group_sync(bar, nthr);
+    const int any = gs.flag[g];
+    const T rm = (T)__uint_as_float(gs.rbits[g]);
+    group_sync(bar, nthr);
+    if (!any || rm < stop) return sweep;
+  }
+  return -1;
+}
+
+// Warp groups for one wave of charge blocks: every block gets at least one
+// warp, then warps go one at a time to the block whose sweep takes longest
+// ((p - 1) rounds of ceil(p / (2 w)) pairs per warp), never beyond p / 2.
+// nblk <= 15 and nblk <= nwarps.  Writes the first warp and the warp count
+// of every block.  One thread.
+__device__ inline void assign_warps(const int* p, int nblk, int nwarps, int* w0, int* nw) {
+  int used = 0;
+  for (int b = 0; b < nblk; ++b) nw[b] = 1, ++used;
+  while (used < nwarps) {
+    int best = -1;
+    long long bt = -1;
+    for (int b = 0; b < nblk; ++b) {
+      const int cap = (p[b] + 1) / 2;
+      if (nw[b] >= cap) continue;
+      const long long t = (long long)(p[b] - 1) * ((p[b] + 2 * nw[b] - 1) / (2 * nw[b]));
+      if (t > bt) bt = t, best = b;
+    }
+    if (best < 0) break;
+    ++nw[best];
+    ++used;
+  }
+  int w = 0;
+  for (int b = 0; b < nblk; ++b) w0[b] = w, w += nw[b];
+}
+
+// One wave of a split's charge blocks: blocks [b0, b0 + n) decomposed at
+// once, block i by warps [w0[i], w0[i] + nw[i]) (barrier id i + 1).
+struct WaveSh {
+  int32_t b0, n;
+  int32_t w0[15], nw[15], sw[15];
+  int32_t off[15];                        // shared-memory offset (elements) of block i
+};
+
+// Index of this warp's group in the wave, or -1 (an idle warp).
+__device__ __forceinline__ int my_group(const WaveSh& wv, int warp) {
+  for (int i = 0; i < wv.n; ++i)
+    if (warp >= wv.w0[i] && warp < wv.w0[i] + wv.nw[i]) return i;
+  return -1;
 }
 
 __device__ __forceinline__ double warp_sum64(double v) {

@@ -395,28 +395,52 @@ __device__ void two_site_op(ChainDev* c, const OpDev op, int t, Shared& sh, int3
 
 // One two-site op of a chain, block by block in the S^z charge of the new
 // middle bond (Sec. II.C): theta by block GEMMs, the gate within its
-// conserved sectors, a binary64 one-sided Jacobi per block, then one
-// truncation over the union of the blocks' singular values (Sec. II).
+// conserved sectors, a binary64 one-sided Jacobi per block (the blocks of a
+// split at once, each by its own warp group), then one truncation over the
+// union of the blocks' singular values (Sec. II).
 __device__ void two_site_op_blocked(ChainDev* c, const OpDev op, int t, Shared& sh, blk::SplitSh& ss,
-                                    int32_t* ctx_err) {
+                                    blk::WaveSh& wv, blk::GroupSh& gs, int32_t* ctx_err) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (!blk::prepare<NT>(c, op, ss)) blk::prepare<NT>(c, op, ss);
   blk::theta_blocks<NT, TM, TN, TK, double>(c, op.k, ss, c->theta, &sh.g.a[0][0]);
   const blk::Meta* M = reinterpret_cast<const blk::Meta*>(c->meta);
   int sweeps = 0;
   int64_t cost = -1;
-  for (int b = 0; b < ss.nblk; ++b) {
-    const blk::BlockRec& r = M->b[b];
-    double* W = c->W + r.woff;
-    double* V = c->V + r.voff;
-    blk::gather_block<NT, double, double>(c, op.k, ss, r, c->theta, W, r.q, V, r.p);
-    __syncthreads();
-    const int sw = blk::jacobi64<NT>(W, r.q, r.p, V, c->sig, 1e-9, kMaxSweeps, &sh.ival[0], &sh.scal[5]);
-    if (sw < 0) {
-      set_error(c, HM_ERR_NUMERIC, t, ctx_err);
-      return;
+  for (int b0 = 0; b0 < ss.nblk;) {
+    if (tid == 0) {
+      int p[15];
+      int n = 0;
+      while (b0 + n < ss.nblk && n < 15 && n < NT / 32) p[n] = M->b[b0 + n].p, ++n;
+      wv.b0 = b0;
+      wv.n = n;
+      blk::assign_warps(p, n, NT / 32, wv.w0, wv.nw);
     }
-    const int64_t cb = (int64_t)r.q * r.p * r.p;   // sweeps of the costliest block
-    if (cb > cost) cost = cb, sweeps = sw;
+    __syncthreads();
+    const int n = wv.n;
+    for (int i = 0; i < n; ++i) {
+      const blk::BlockRec& r = M->b[b0 + i];
+      blk::gather_block<NT, double, double>(c, op.k, ss, r, c->theta, c->W + r.woff, r.q, c->V + r.voff, r.p);
+    }
+    __syncthreads();
+    const int g = blk::my_group(wv, warp);
+    if (g >= 0) {
+      const blk::BlockRec& r = M->b[b0 + g];
+      const int sw = blk::jacobi_group<double>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig + r.svoff,
+                                               warp - wv.w0[g], wv.nw[g], g + 1, g, gs, 1e-9, kMaxSweeps);
+      if (warp == wv.w0[g] && (tid & 31) == 0) wv.sw[g] = sw;
+    }
+    __syncthreads();
+    for (int i = 0; i < n; ++i) {
+      if (wv.sw[i] < 0) {
+        set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+        return;
+      }
+      const blk::BlockRec& r = M->b[b0 + i];
+      const int64_t cb = (int64_t)r.q * r.p * r.p;   // sweeps of the costliest block
+      if (cb > cost) cost = cb, sweeps = wv.sw[i];
+    }
+    b0 += n;
+    __syncthreads();
   }
   blk::finish<NT>(c, op, t, ss, c->theta, ctx_err, sweeps, 0);
   if (threadIdx.x == 0 && ss.kk > 0) {
@@ -439,6 +463,8 @@ __device__ void two_site_op_blocked(ChainDev* c, const OpDev op, int t, Shared& 
 __global__ void __launch_bounds__(NT) evolve_fp64_kernel(BatchArg b, OutArg o) {
   __shared__ Shared sh;
   __shared__ blk::SplitSh ss;
+  __shared__ blk::WaveSh wv;
+  __shared__ blk::GroupSh gs;
   ChainDev* c = b.c[blockIdx.x];
   const OpDev* ops = b.ops_override ? b.ops_override : c->ops;
   const int n_ops = b.ops_override ? b.n_override : c->n_ops;
@@ -446,7 +472,7 @@ __global__ void __launch_bounds__(NT) evolve_fp64_kernel(BatchArg b, OutArg o) {
   for (int t = b.t0; t < t1; ++t) {
     if (*(volatile int32_t*)c->status != 0) return;
     __syncthreads();
-    two_site_op_blocked(c, ops[t], t, sh, ss, o.ctx_err);
+    two_site_op_blocked(c, ops[t], t, sh, ss, wv, gs, o.ctx_err);
     __syncthreads();
   }
 }
@@ -479,14 +505,6 @@ __device__ __constant__ double kSz[9] = {1, 0, 0, 0, 0, 0, 0, 0, -1};
 // S+ = sqrt(2) (|+1><0| + |0><-1|); S- its transpose (basis m = +1, 0, -1)
 __device__ __constant__ double kSp[9] = {0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0, 0, 0};
 __device__ __constant__ double kSm[9] = {0, 0, 0, 1.4142135623730951, 0, 0, 0, 1.4142135623730951, 0};
-// S^x = (S+ + S-)/2 and A = (S+ - S-)/2 = i S^y, so S^y_i S^y_j = -A_i A_j.
-__device__ __constant__ double kSx[9] = {0, 0.7071067811865476, 0, 0.7071067811865476, 0, 0.7071067811865476,
-                                         0, 0.7071067811865476, 0};
-__device__ __constant__ double kAy[9] = {0, 0.7071067811865476, 0, -0.7071067811865476, 0, 0.7071067811865476,
-                                         0, -0.7071067811865476, 0};
-__device__ __constant__ double kAyNeg[9] = {0, -0.7071067811865476, 0, 0.7071067811865476, 0, -0.7071067811865476,
-                                            0, 0.7071067811865476, 0};
-
 // Right environment through one site: Rout[i, j] = sum_s A^s Rin A^{sT}
 // (Rin cr x cr, Rout cl x cl).  Y: 3cl x cr scratch.
 __device__ void cta_rtransfer(const double* Rin, const double* A, int cl, int cr, double* Rout, double* Y,
@@ -494,6 +512,113 @@ __device__ void cta_rtransfer(const double* Rin, const double* A, int cl, int cr
   if (threadIdx.x == 0) sh.scal[4] += 12.0 * cl * cr * cr;
   cta_gemm<false, false>(3 * cl, cr, cr, 1.0, A, cr, Rin, cr, 0.0, Y, cr, sh.g);
   cta_gemm<false, true>(cl, cl, 3 * cr, 1.0, Y, 3 * cr, A, 3 * cr, 0.0, Rout, cl, sh.g);
+}
+
+// Charge blocks of the transfer matrices (Sec. II.C).  A bond's indices are
+// grouped by S^z charge, so a charge is one run [start, start + len) of the
+// bond.  For a state of definite total S^z an environment E[i, j] (bra i,
+// ket j) is nonzero only where q_i - q_j = D, its charge shift: 0 for the
+// plain environment, sigma for one S^+ inserted on a leg of sign sigma,
+// -sigma for S^-.  Dense-mode chains have every charge 0: one run, D = 0,
+// and these reduce to the plain dense transfers.
+__device__ void charge_run(const int16_t* q, int n, int Q, int* start, int* len) {
+  int lo = 0, hi = n;
+  while (lo < hi) {                       // first index with q >= Q
+    const int mid = (lo + hi) >> 1;
+    if (q[mid] < Q) lo = mid + 1;
+    else hi = mid;
+  }
+  int e = lo;
+  while (e < n && q[e] == Q) ++e;
+  *start = lo;
+  *len = e - lo;
+}
+
+// Left environment through site pos with operator O (nullptr: identity;
+// O[s][t] = <s|O|t>, nonzero only for m(s) - m(t) = dO):
+// Eout[i', j'] = sum_{s,t} O[s][t] sum_{i,j} A[i,s,i'] Ein[i,j] A[j,t,j'],
+// computed only on the charge blocks it can fill.  Ein has shift D; the
+// result has shift D + sigma dO (returned).  Z: scratch of cl x cr doubles.
+__device__ int cta_transfer_blk(const ChainDev* c, int pos, const double* Ein, int D, const double* O, int dO,
+                                double* Eout, double* Z, Shared& sh) {
+  const int cl = c->chi[pos], cr = c->chi[pos + 1];
+  const double* A = c->site[pos];
+  const int16_t* qL = c->qn + (size_t)pos * c->chi_cap;
+  const int16_t* qR = qL + c->chi_cap;
+  const int sg = c->sgn[pos];
+  const int D2 = D + sg * dO;
+  for (int e = threadIdx.x; e < cr * cr; e += NT) Eout[e] = 0.0;
+  __syncthreads();
+  double fl = 0.0;
+  for (int b0 = 0; b0 < cr;) {
+    int bs, bl;
+    charge_run(qR, cr, qR[b0], &bs, &bl);     // bra run of the right bond
+    const int Qb = qR[b0], Qk = Qb - D2;
+    b0 = bs + bl;
+    int ks, kl;
+    charge_run(qR, cr, Qk, &ks, &kl);         // ket run
+    if (kl == 0) continue;
+    for (int s1 = 0; s1 < 3; ++s1) {
+      int is, il;
+      charge_run(qL, cl, Qb - sg * (1 - s1), &is, &il);
+      if (il == 0) continue;
+      bool first = true;
+      for (int t1 = 0; t1 < 3; ++t1) {
+        const double w = O ? O[3 * s1 + t1] : (s1 == t1 ? 1.0 : 0.0);
+        if (w == 0.0) continue;
+        int js, jl;
+        charge_run(qL, cl, Qk - sg * (1 - t1), &js, &jl);
+        if (jl == 0) continue;
+        // Z (il x kl) (+)= w Ein[i-run, j-run] A[j-run, t1, k-run]
+        cta_gemm<false, false>(il, kl, jl, w, Ein + (size_t)is * cl + js, cl, A + (size_t)(3 * js + t1) * cr + ks,
+                               3 * cr, first ? 0.0 : 1.0, Z, kl, sh.g);
+        fl += 2.0 * il * jl * kl;
+        first = false;
+      }
+      if (first) continue;
+      // Eout[b-run, k-run] += A[i-run, s1, b-run]^T Z
+      cta_gemm<true, false>(bl, kl, il, 1.0, A + (size_t)(3 * is + s1) * cr + bs, 3 * cr, Z, kl, 1.0,
+                            Eout + (size_t)bs * cr + ks, cr, sh.g);
+      fl += 2.0 * il * bl * kl;
+    }
+  }
+  if (threadIdx.x == 0) sh.scal[4] += fl;
+  __syncthreads();
+  return D2;
+}
+
+// Plain right environment through site pos (shift 0):
+// Rout[i, j] = sum_s sum_{a,b} A[i,s,a] Rin[a,b] A[j,s,b], block by block.
+// Y: scratch of cl x cr doubles.
+__device__ void cta_rtransfer_blk(const ChainDev* c, int pos, const double* Rin, double* Rout, double* Y, Shared& sh) {
+  const int cl = c->chi[pos], cr = c->chi[pos + 1];
+  const double* A = c->site[pos];
+  const int16_t* qL = c->qn + (size_t)pos * c->chi_cap;
+  const int16_t* qR = qL + c->chi_cap;
+  const int sg = c->sgn[pos];
+  for (int e = threadIdx.x; e < cl * cl; e += NT) Rout[e] = 0.0;
+  __syncthreads();
+  double fl = 0.0;
+  for (int i0 = 0; i0 < cl;) {
+    int is, il;
+    charge_run(qL, cl, qL[i0], &is, &il);
+    const int Q = qL[i0];
+    i0 = is + il;
+    for (int s1 = 0; s1 < 3; ++s1) {
+      int as, al;
+      charge_run(qR, cr, Q + sg * (1 - s1), &as, &al);
+      if (al == 0) continue;
+      // Y (il x al) = A[i-run, s1, a-run] Rin[a-run, a-run]
+      cta_gemm<false, false>(il, al, al, 1.0, A + (size_t)(3 * is + s1) * cr + as, 3 * cr, Rin + (size_t)as * cr + as,
+                             cr, 0.0, Y, al, sh.g);
+      // Rout[i-run, i-run] += Y A[i-run, s1, a-run]^T
+      cta_gemm<false, true>(il, il, al, 1.0, Y, al, A + (size_t)(3 * is + s1) * cr + as, 3 * cr, 1.0,
+                            Rout + (size_t)is * cl + is, cl, sh.g);
+      fl += 2.0 * il * al * al + 2.0 * il * il * al;
+    }
+  }
+  if (threadIdx.x == 0) sh.scal[4] += fl;
+  __syncthreads();
 }
 
 // sum_{k,l} X[k, l] Y[k, l] over n entries, block-wide.
@@ -540,7 +665,7 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
       }
     }
     __syncthreads();
-    cta_rtransfer(Rp[rc], c->site[pos], c->chi[pos], c->chi[pos + 1], Rp[rc ^ 1], Z, sh);
+    cta_rtransfer_blk(c, pos, Rp[rc], Rp[rc ^ 1], Z, sh);
     rc ^= 1;
   }
   const double nrm = Rp[rc][0];            // <psi|psi>
@@ -549,12 +674,14 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
   int pos = 0, cur = 0;
   double E_est = 0.0;
   // A chain in frame 1 stores R^N |psi> (R exchanges S^x and S^z, R S^z R =
-  // S^x): there <Sz_i Sz_j> of |psi> is <Sx_i Sx_j> of the stored state, and
-  // S_i.S_j is invariant.  Frame 0: (Sz Sz, S+ S-, S- S+); frame 1:
-  // (Sx Sx, Sz Sz, A (-A)), whose sum is S.S.
+  // S^x): there <Sz_i Sz_j> of |psi> is <Sx_i Sx_j> of the stored state,
+  // which for a state of definite total S^z is (<S+_i S-_j> + <S-_i S+_j>)/4;
+  // S_i.S_j is invariant.  Passes: (Sz Sz), (S+ S-), (S- S+); operator
+  // charge shifts dO = 0, +1, -1 and -dO.
   const int frame = c->counters[2];
-  const double* ops1[3] = {frame ? kSx : kSz, frame ? kSz : kSp, frame ? kAy : kSm};
-  const double* ops2[3] = {frame ? kSx : kSz, frame ? kSz : kSm, frame ? kAyNeg : kSp};
+  const double* ops1[3] = {kSz, kSp, kSm};
+  const double* ops2[3] = {kSz, kSm, kSp};
+  const int dop[3] = {0, 1, -1};
   int bi = 0;
   while (bi < c->n_meas) {
     const int a = c->meas_i[bi];
@@ -562,33 +689,33 @@ __global__ void __launch_bounds__(NT) measure_fp64_kernel(BatchArg b, OutArg o) 
     while (bend < c->n_meas && c->meas_i[bend] == a) ++bend;
     const int blast = c->meas_j[bend - 1];
     while (pos < a) {
-      cta_transfer(Lp[cur], c->site[pos], c->chi[pos], c->chi[pos + 1], nullptr, Lp[cur ^ 1], Z, sh);
+      cta_transfer_blk(c, pos, Lp[cur], 0, nullptr, 0, Lp[cur ^ 1], Z, sh);
       cur ^= 1;
       ++pos;
     }
     double vals[3][8];   // up to 8 bonds per start site
     for (int o1 = 0; o1 < 3; ++o1) {
       int ec = 0;
-      cta_transfer(Lp[cur], c->site[a], c->chi[a], c->chi[a + 1], ops1[o1], Ep[ec], Z, sh);
+      int D = cta_transfer_blk(c, a, Lp[cur], 0, ops1[o1], dop[o1], Ep[ec], Z, sh);
       for (int kk = a + 1; kk <= blast; ++kk) {
         for (int q = bi; q < bend; ++q) {
           if (c->meas_j[q] == kk) {
-            cta_transfer(Ep[ec], c->site[kk], c->chi[kk], c->chi[kk + 1], ops2[o1], Et, Z, sh);
+            cta_transfer_blk(c, kk, Ep[ec], D, ops2[o1], -dop[o1], Et, Z, sh);
             const int n2 = c->chi[kk + 1] * c->chi[kk + 1];
             vals[o1][q - bi] = cta_dot(Et, Rend + (size_t)c->meas_slot[q] * cc, n2, sh);
           }
         }
         if (kk < blast) {
-          cta_transfer(Ep[ec], c->site[kk], c->chi[kk], c->chi[kk + 1], nullptr, Ep[ec ^ 1], Z, sh);
+          D = cta_transfer_blk(c, kk, Ep[ec], D, nullptr, 0, Ep[ec ^ 1], Z, sh);
           ec ^= 1;
         }
       }
     }
     if (tid == 0) {
       for (int q = bi; q < bend; ++q) {
-        const double zz = vals[0][q - bi] / nrm;
-        const double ss = frame ? zz + (vals[1][q - bi] + vals[2][q - bi]) / nrm
-                                : zz + 0.5 * (vals[1][q - bi] + vals[2][q - bi]) / nrm;
+        const double pm = (vals[1][q - bi] + vals[2][q - bi]) / nrm;
+        const double ss = vals[0][q - bi] / nrm + 0.5 * pm;
+        const double zz = frame ? 0.25 * pm : vals[0][q - bi] / nrm;
         out[1 + 2 * q] = ss;
         out[2 + 2 * q] = zz;
         E_est += c->meas_J[q] * ss;

@@ -320,88 +320,6 @@ __device__ int cta_jacobi_f32(float* W, int q, int p, float* V, int b, float* sm
   return converged ? done : -1;
 }
 
-// One-sided Jacobi in binary32 on a charge block held entirely in shared
-// memory: W (q x p column-major, leading dimension ldw), V (p x p, leading
-// dimension ldv, holds the starting basis), column norms cached in nrm and
-// recomputed at every sweep start.  Round-robin pairing, one warp per pair.
-// Same stopping rule as cta_jacobi_f32.  Returns the sweeps, or -1.
-__device__ int jacobi32_smem(float* W, int q, int ldw, int p, float* V, int ldv, float* nrm, Scal& sc) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int nwarps = NT / 32;
-  const float tol = sqrtf((float)q) * FLT_EPSILON;
-  const int p2 = p + (p & 1);
-  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
-    for (int j = warp; j < p; j += nwarps) {
-      const float* cj = W + (size_t)j * ldw;
-      float s2 = 0.f;
-      for (int i = lane; i < q; i += 32) s2 = fmaf(cj[i], cj[i], s2);
-      s2 = warp_sumf(s2);
-      if (lane == 0) nrm[j] = s2;
-    }
-    if (tid == 0) {
-      sc.ival[0] = 0;
-      sc.ival[2] = 0;
-    }
-    __syncthreads();
-    int rot = 0;
-    float rmax = 0.f;
-    for (int rd = 0; rd < p2 - 1; ++rd) {
-      for (int pi = warp; pi < p2 / 2; pi += nwarps) {
-        int a, b;
-        if (pi == 0) {
-          a = rd;
-          b = p2 - 1;
-        } else {
-          a = (rd + pi) % (p2 - 1);
-          b = (rd - pi + (p2 - 1)) % (p2 - 1);
-        }
-        if (a >= p || b >= p) continue;
-        float* x = W + (size_t)a * ldw;
-        float* y = W + (size_t)b * ldw;
-        float ga = 0.f;
-        for (int i = lane; i < q; i += 32) ga = fmaf(x[i], y[i], ga);
-        ga = warp_sumf(ga);
-        const float al = nrm[a], be = nrm[b];
-        if (ga != 0.f && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
-          rmax = fmaxf(rmax, fabsf(ga) / (sqrtf(al) * sqrtf(be)));
-          const float zeta = (be - al) / (2.f * ga);
-          float t;
-          if (fabsf(zeta) > 1e18f) t = 0.5f / zeta;
-          else t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float cs = rsqrtf(1.f + t * t), sn = cs * t;
-          for (int i = lane; i < q; i += 32) {
-            const float u = x[i], v = y[i];
-            x[i] = cs * u - sn * v;
-            y[i] = sn * u + cs * v;
-          }
-          float* vx = V + (size_t)a * ldv;
-          float* vy = V + (size_t)b * ldv;
-          for (int i = lane; i < p; i += 32) {
-            const float u = vx[i], v = vy[i];
-            vx[i] = cs * u - sn * v;
-            vy[i] = sn * u + cs * v;
-          }
-          __syncwarp();
-          if (lane == 0) {
-            nrm[a] = al - t * ga;
-            nrm[b] = be + t * ga;
-          }
-          rot = 1;
-        }
-      }
-      __syncthreads();
-    }
-    if (rot && lane == 0) sc.ival[0] = 1;
-    if (lane == 0) atomicMax(&sc.ival[2], __float_as_int(rmax));
-    __syncthreads();
-    const int any = sc.ival[0];
-    const float rm = __int_as_float(sc.ival[2]);
-    __syncthreads();
-    if (!any || rm < 2e-4f) return sweep;
-  }
-  return -1;
-}
-
 __device__ void set_error(const ChainDev* c, int code, int where, int32_t* ctx_err) {
   if (threadIdx.x == 0) {
     if (atomicCAS(c->status, 0, code) == 0) *c->err_where = where;
@@ -419,61 +337,119 @@ constexpr double kPolishStop = 1e-7;
 
 // One two-site op (step 2 of Sec. I.C.1) in charge blocks (Sec. II.C):
 // theta and the gate in binary32 (operands rounded from the binary64 site
-// tensors, binary32 accumulation); per block a binary32 one-sided Jacobi in
-// shared memory (global memory with staged column blocks when the block does
-// not fit) as a preconditioner, then binary64 sweeps on the promoted W and V
-// until the binary64 stopping rule holds, so the singular values and the
-// kept vectors are binary64-accurate for that theta; then the truncation
-// rule (Sec. II), renormalisation and absorb in binary64.
+// tensors, binary32 accumulation, gate coefficients as binary32 pairs); the
+// blocks of a split in waves that fit in shared memory, each block of a wave
+// decomposed by its own warp group at the same time: a binary32 one-sided
+// Jacobi as a preconditioner, then binary64 sweeps on the promoted W and V
+// until the binary64 stopping rule holds, so the singular values and the kept
+// vectors are binary64-accurate for that theta.  A block too large for
+// shared memory runs alone, its binary32 sweeps on column blocks staged from
+// global memory.  Then the truncation rule (Sec. II), renormalisation and
+// absorb in binary64.
 __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols, float* smem, Scal& sc,
-                                  blk::SplitSh& ss, int32_t* ctx_err) {
+                                  blk::SplitSh& ss, blk::WaveSh& wv, blk::GroupSh& gs, int32_t* ctx_err) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (!blk::prepare<NT>(c, op, ss)) blk::prepare<NT>(c, op, ss);
   float* theta = reinterpret_cast<float*>(c->theta);
   blk::theta_blocks<NT, GM, GN, GK, float>(c, op.k, ss, theta, smem);
   const blk::Meta* M = reinterpret_cast<const blk::Meta*>(c->meta);
   int sw32 = 0, sw64 = 0;
   int64_t cost = -1;
-  for (int b = 0; b < ss.nblk; ++b) {
-    const blk::BlockRec& r = M->b[b];
-    const int q = r.q, p = r.p;
-    const int ldw = q | 1, ldv = p | 1;         // odd strides: conflict-free column walks
-    const size_t need = ((size_t)p * ldw + (size_t)p * ldv + (size_t)p) * sizeof(float);
-    float* W32;
-    float* V32;
-    int lw, lv, sw;
-    if (need <= kBlockSmem) {
-      W32 = smem;
-      V32 = smem + (size_t)p * ldw;
-      blk::gather_block<NT, float, float>(c, op.k, ss, r, theta, W32, ldw, V32, ldv);
-      __syncthreads();
-      sw = jacobi32_smem(W32, q, ldw, p, V32, ldv, V32 + (size_t)p * ldv, sc);
-      lw = ldw;
-      lv = ldv;
-    } else {
-      W32 = c->X;
-      V32 = c->X + (size_t)q * p;
-      blk::gather_block<NT, float, float>(c, op.k, ss, r, theta, W32, q, V32, p);
-      __syncthreads();
-      sw = cta_jacobi_f32(W32, q, p, V32, bcols, smem, sc, nullptr);
-      lw = q;
-      lv = p;
+  constexpr int64_t cap = (int64_t)(kBlockSmem / sizeof(float));
+  for (int b0 = 0; b0 < ss.nblk;) {
+    if (tid == 0) {
+      // as many consecutive blocks as fit in shared memory (at most 15 and
+      // one warp each); a block that does not fit alone takes the global path
+      int64_t used = 0;
+      int n = 0, p[15];
+      while (b0 + n < ss.nblk && n < 15 && n < NT / 32) {
+        const blk::BlockRec& r = M->b[b0 + n];
+        const int64_t need = (int64_t)r.p * (r.q | 1) + (int64_t)r.p * (r.p | 1) + r.p;
+        if (used + need > cap) break;
+        wv.off[n] = (int32_t)used;
+        p[n] = r.p;
+        used += need;
+        ++n;
+      }
+      wv.b0 = b0;
+      wv.n = n;
+      if (n > 0) blk::assign_warps(p, n, NT / 32, wv.w0, wv.nw);
     }
-    if (sw < 0) {
-      set_error(c, HM_ERR_NUMERIC, t, ctx_err);
-      return;
-    }
-    double* W64 = c->W + r.woff;
-    double* V64 = c->V + r.voff;
-    for (int e = threadIdx.x; e < q * p; e += NT) W64[e] = (double)W32[(size_t)(e / q) * lw + e % q];
-    for (int e = threadIdx.x; e < p * p; e += NT) V64[e] = (double)V32[(size_t)(e / p) * lv + e % p];
     __syncthreads();
-    const int s64 = blk::jacobi64<NT>(W64, q, p, V64, c->sig, kPolishStop, kMaxSweeps, &sc.ival[0], &sc.dval[1]);
-    if (s64 < 0) {
-      set_error(c, HM_ERR_NUMERIC, t, ctx_err);
-      return;
+    const int n = wv.n;
+    if (n == 0) {
+      const blk::BlockRec& r = M->b[b0];
+      float* W32 = c->X;
+      float* V32 = c->X + (size_t)r.q * r.p;
+      blk::gather_block<NT, float, float>(c, op.k, ss, r, theta, W32, r.q, V32, r.p);
+      __syncthreads();
+      const int sw = cta_jacobi_f32(W32, r.q, r.p, V32, bcols, smem, sc, nullptr);
+      if (sw < 0) {
+        set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+        return;
+      }
+      double* W64 = c->W + r.woff;
+      double* V64 = c->V + r.voff;
+      for (int e = tid; e < r.q * r.p; e += NT) W64[e] = (double)W32[e];
+      for (int e = tid; e < r.p * r.p; e += NT) V64[e] = (double)V32[e];
+      __syncthreads();
+      const int s64 = blk::jacobi64<NT>(W64, r.q, r.p, V64, c->sig, kPolishStop, kMaxSweeps, &sc.ival[0], &sc.dval[1]);
+      if (s64 < 0) {
+        set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+        return;
+      }
+      const int64_t cb = (int64_t)r.q * r.p * r.p;
+      if (cb > cost) cost = cb, sw32 = sw, sw64 = s64;
+      b0 += 1;
+      continue;
     }
-    const int64_t cb = (int64_t)q * p * p;
-    if (cb > cost) cost = cb, sw32 = sw, sw64 = s64;
+    for (int i = 0; i < n; ++i) {
+      const blk::BlockRec& r = M->b[b0 + i];
+      float* W32 = smem + wv.off[i];
+      float* V32 = W32 + (size_t)r.p * (r.q | 1);
+      blk::gather_block<NT, float, float>(c, op.k, ss, r, theta, W32, r.q | 1, V32, r.p | 1);
+    }
+    __syncthreads();
+    const int g = blk::my_group(wv, warp);
+    if (g >= 0) {
+      const blk::BlockRec& r = M->b[b0 + g];
+      float* W32 = smem + wv.off[g];
+      float* V32 = W32 + (size_t)r.p * (r.q | 1);
+      const int sw = blk::jacobi_group<float>(W32, r.q, r.q | 1, r.p, V32, r.p | 1, V32 + (size_t)r.p * (r.p | 1),
+                                              warp - wv.w0[g], wv.nw[g], g + 1, g, gs, 2e-4f, kMaxSweeps);
+      if (warp == wv.w0[g] && (tid & 31) == 0) wv.sw[g] = sw;
+    }
+    __syncthreads();
+    for (int i = 0; i < n; ++i) {
+      const blk::BlockRec& r = M->b[b0 + i];
+      const float* W32 = smem + wv.off[i];
+      const float* V32 = W32 + (size_t)r.p * (r.q | 1);
+      double* W64 = c->W + r.woff;
+      double* V64 = c->V + r.voff;
+      for (int e = tid; e < r.q * r.p; e += NT) W64[e] = (double)W32[(size_t)(e / r.q) * (r.q | 1) + e % r.q];
+      for (int e = tid; e < r.p * r.p; e += NT) V64[e] = (double)V32[(size_t)(e / r.p) * (r.p | 1) + e % r.p];
+    }
+    __syncthreads();
+    if (g >= 0) {
+      // binary64 polish by the same groups; norms of block g in c->sig
+      const blk::BlockRec& r = M->b[b0 + g];
+      const int s64 = blk::jacobi_group<double>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig + r.svoff,
+                                                warp - wv.w0[g], wv.nw[g], g + 1, g, gs, kPolishStop, kMaxSweeps);
+      if (warp == wv.w0[g] && (tid & 31) == 0) wv.sw[g] = wv.sw[g] < 0 ? -1 : (s64 < 0 ? -1 : wv.sw[g] + 1000 * s64);
+    }
+    __syncthreads();
+    for (int i = 0; i < n; ++i) {
+      const int code = wv.sw[i];
+      if (code < 0) {
+        set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+        return;
+      }
+      const blk::BlockRec& r = M->b[b0 + i];
+      const int64_t cb = (int64_t)r.q * r.p * r.p;
+      if (cb > cost) cost = cb, sw32 = code % 1000, sw64 = code / 1000;
+    }
+    b0 += n;
+    __syncthreads();
   }
   blk::finish<NT>(c, op, t, ss, c->theta, ctx_err, sw32, sw64);
   if (threadIdx.x == 0 && ss.kk > 0) {
@@ -497,6 +473,8 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
   extern __shared__ float smem[];
   __shared__ Scal sc;
   __shared__ blk::SplitSh ss;
+  __shared__ blk::WaveSh wv;
+  __shared__ blk::GroupSh gs;
   ChainDev* c = b.c[blockIdx.x];
   const OpDev* ops = b.ops_override ? b.ops_override : c->ops;
   const int n_ops = b.ops_override ? b.n_override : c->n_ops;
@@ -504,7 +482,7 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
   for (int t = b.t0; t < t1; ++t) {
     if (*(volatile int32_t*)c->status != 0) return;
     __syncthreads();
-    two_site_op_mixed(c, ops[t], t, bcols, smem, sc, ss, o.ctx_err);
+    two_site_op_mixed(c, ops[t], t, bcols, smem, sc, ss, wv, gs, o.ctx_err);
     __syncthreads();
   }
 }

@@ -24,6 +24,7 @@
 #define __device__
 #define __shared__ static
 #define __launch_bounds__(...)
+#define HM_HOST_EMULATION 1
 
 namespace simt {
 struct Idx {
@@ -35,6 +36,7 @@ Idx bdim();
 Idx gdim();
 void sync();
 void syncwarp();
+void named_sync(int id, int count);     // bar.sync id, count (count in threads)
 uint64_t exchange(uint64_t bits, int lane_xor);
 void* dynamic_smem();
 void launch(unsigned grid, unsigned block, size_t smem, const std::function<void()>& body);
@@ -69,6 +71,16 @@ inline int __float_as_int(float f) {
   std::memcpy(&r, &f, sizeof r);
   return r;
 }
+inline unsigned __float_as_uint(float f) {
+  unsigned r;
+  std::memcpy(&r, &f, sizeof r);
+  return r;
+}
+inline float __uint_as_float(unsigned i) {
+  float r;
+  std::memcpy(&r, &i, sizeof r);
+  return r;
+}
 inline float __int_as_float(int i) {
   float r;
   std::memcpy(&r, &i, sizeof r);
@@ -97,6 +109,13 @@ inline int atomicMin(int* p, int value) {
   }
   return old;
 }
+inline unsigned atomicMax(unsigned* p, unsigned value) {
+  std::atomic_ref<unsigned> r(*p);
+  unsigned old = r.load();
+  while (old < value && !r.compare_exchange_weak(old, value)) {
+  }
+  return old;
+}
 inline unsigned long long atomicMax(unsigned long long* p, unsigned long long value) {
   std::atomic_ref<unsigned long long> r(*p);
   unsigned long long old = r.load();
@@ -105,8 +124,13 @@ inline unsigned long long atomicMax(unsigned long long* p, unsigned long long va
   return old;
 }
 
-// Global-namespace functions device code sees.
+// Global-namespace functions device code sees (float and double overloads).
 using std::isfinite;
+using std::copysign;
+using std::fabs;
+using std::fma;
+using std::fmax;
+using std::sqrt;
 inline int min(int a, int b) { return a < b ? a : b; }
 inline int max(int a, int b) { return a > b ? a : b; }
 inline unsigned min(unsigned a, unsigned b) { return a < b ? a : b; }

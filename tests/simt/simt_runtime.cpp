@@ -29,13 +29,14 @@
 namespace simt {
 namespace {
 
-enum State { RUNNABLE, AT_BLOCK, AT_WARP, DONE };
+enum State { RUNNABLE, AT_BLOCK, AT_WARP, AT_NAMED, DONE };
 
 struct Fiber {
   ucontext_t ctx;
   std::unique_ptr<char[]> stack;
   State state = RUNNABLE;
   Idx tid{0, 0, 0};
+  int bar_id = 0, bar_count = 0;      // named barrier this fiber waits at
 };
 
 constexpr size_t kStack = 256 * 1024;
@@ -72,6 +73,24 @@ bool release() {
       if (f.state == AT_BLOCK) f.state = RUNNABLE;
     return true;
   }
+  // a named barrier (id, count) opens when `count` fibers wait at it
+  for (int id = 1; id < 16; ++id) {
+    int waiting = 0, count = -1;
+    for (const Fiber& f : g_fibers)
+      if (f.state == AT_NAMED && f.bar_id == id) {
+        ++waiting;
+        if (count >= 0 && f.bar_count != count) {
+          std::fprintf(stderr, "simt: named barrier %d waited on with counts %d and %d\n", id, count, f.bar_count);
+          std::abort();
+        }
+        count = f.bar_count;
+      }
+    if (waiting > 0 && waiting == count) {
+      for (Fiber& f : g_fibers)
+        if (f.state == AT_NAMED && f.bar_id == id) f.state = RUNNABLE;
+      any = true;
+    }
+  }
   const size_t n = g_fibers.size();
   for (size_t w0 = 0; w0 < n; w0 += 32) {
     bool all = true, some = false;
@@ -97,6 +116,11 @@ Idx bdim() { return g_bdim; }
 Idx gdim() { return g_gdim; }
 void sync() { wait(AT_BLOCK); }
 void syncwarp() { wait(AT_WARP); }
+void named_sync(int id, int count) {
+  g_cur->bar_id = id;
+  g_cur->bar_count = count;
+  wait(AT_NAMED);
+}
 uint64_t exchange(uint64_t bits, int lane_xor) {
   const unsigned t = g_cur->tid.x, w0 = t & ~31u;
   g_xbuf[t] = bits;
