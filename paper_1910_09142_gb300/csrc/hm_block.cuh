@@ -402,21 +402,24 @@ struct GroupSh {
 // group, barrier id bar): W (q x p column-major, q >= p, leading dimension
 // ldw), rotations accumulated into V (p x p, leading dimension ldv, holds the
 // starting basis), column norms cached in nrm and recomputed at every sweep
-// start.  Round-robin pairing (every round's pairs are disjoint), one warp
-// per pair.  Stops after a sweep with no rotation or whose largest ratio
-// |g| / sqrt(a b) is below `stop` (the next sweep's off-diagonals are then of
-// order stop^2).  Several groups run different charge blocks at once, so a
-// split's blocks share the CTA instead of taking turns.  Returns the sweeps,
-// or -1 when max_sweeps ran out.
-template <typename T>
-__device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, T* __restrict__ V, int ldv,
+// start.  Round-robin pairing: every round's pairs are disjoint.  L lanes
+// work on one pair, so a warp rotates 32 / L pairs at once (more pairs in
+// flight, shorter reductions; the rotations are latency-bound, not
+// arithmetic-bound).  Stops after a sweep with no rotation or whose largest
+// ratio |g| / sqrt(a b) is below `stop` (the next sweep's off-diagonals are
+// then of order stop^2).  Returns the sweeps, or -1 when max_sweeps ran out.
+template <typename T, int L>
+__device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, T* __restrict__ V, int ldv,
                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
+  constexpr int PPW = 32 / L;              // pairs per warp at once
   const int lane = threadIdx.x & 31;
+  const int sub = lane / L, sl = lane % L;
   const int nthr = 32 * nw;
   const T eps = sizeof(T) == sizeof(double) ? T(2.220446049250313e-16) : T(1.1920928955078125e-07);
   const T tol = sqrt((T)q) * eps;
   const T huge = sizeof(T) == sizeof(double) ? T(1e150) : T(1e18);
   const int p2 = p + (p & 1);
+  const int npair = p2 / 2;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
     for (int j = lw; j < p; j += nw) {
       const T* cj = W + (size_t)j * ldw;
@@ -433,54 +436,78 @@ __device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, T* __restr
     T rmax = T(0);
     int rot = 0;
     for (int rd = 0; rd < p2 - 1; ++rd) {
-      for (int pi = lw; pi < p2 / 2; pi += nw) {
-        int a, b;
-        if (pi == 0) {
-          a = rd;
-          b = p2 - 1;
-        } else {
-          a = (rd + pi) % (p2 - 1);
-          b = (rd - pi + (p2 - 1)) % (p2 - 1);
+      for (int base = lw * PPW; base < npair; base += nw * PPW) {   // warp-uniform
+        const int pi = base + sub;
+        int a = -1, b = -1;
+        if (pi < npair) {
+          if (pi == 0) {
+            a = rd;
+            b = p2 - 1;
+          } else {
+            a = (rd + pi) % (p2 - 1);
+            b = (rd - pi + (p2 - 1)) % (p2 - 1);
+          }
+          if (a >= p || b >= p) a = b = -1;
         }
-        if (a >= p || b >= p) continue;
-        T* x = W + (size_t)a * ldw;
-        T* y = W + (size_t)b * ldw;
-        T ga = T(0);
-        for (int i = lane; i < q; i += 32) ga = fma(x[i], y[i], ga);
-        ga = warp_sum_t(ga);
-        const T al = nrm[a], be = nrm[b];
-        if (ga != T(0) && al > T(0) && be > T(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          rmax = fmax(rmax, fabs(ga) / (sqrt(al) * sqrt(be)));
-          const T zeta = (be - al) / (T(2) * ga);
-          T t;
-          if (fabs(zeta) > huge) t = T(0.5) / zeta;
-          else t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
-          for (int i = lane; i < q; i += 32) {
-            const T u = x[i], v = y[i];
-            x[i] = cs * u - sn * v;
-            y[i] = sn * u + cs * v;
+        T* x = W + (size_t)(a < 0 ? 0 : a) * ldw;
+        T* y = W + (size_t)(b < 0 ? 0 : b) * ldw;
+        T g0 = T(0), g1 = T(0);
+        if (a >= 0) {
+          int i = sl;
+          for (; i + L < q; i += 2 * L) {
+            g0 = fma(x[i], y[i], g0);
+            g1 = fma(x[i + L], y[i + L], g1);
           }
-          T* vx = V + (size_t)a * ldv;
-          T* vy = V + (size_t)b * ldv;
-          for (int i = lane; i < p; i += 32) {
-            const T u = vx[i], v = vy[i];
-            vx[i] = cs * u - sn * v;
-            vy[i] = sn * u + cs * v;
+          if (i < q) g0 = fma(x[i], y[i], g0);
+        }
+        T ga = g0 + g1;
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        bool done = false;
+        T na = T(0), nb = T(0);
+        if (a >= 0) {
+          const T al = nrm[a], be = nrm[b];
+          if (ga != T(0) && al > T(0) && be > T(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+            rmax = fmax(rmax, fabs(ga) / (sqrt(al) * sqrt(be)));
+            const T zeta = (be - al) / (T(2) * ga);
+            T t;
+            if (fabs(zeta) > huge) t = T(0.5) / zeta;
+            else t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+            for (int i = sl; i < q; i += L) {
+              const T u = x[i], v = y[i];
+              x[i] = cs * u - sn * v;
+              y[i] = sn * u + cs * v;
+            }
+            T* vx = V + (size_t)a * ldv;
+            T* vy = V + (size_t)b * ldv;
+            for (int i = sl; i < p; i += L) {
+              const T u = vx[i], v = vy[i];
+              vx[i] = cs * u - sn * v;
+              vy[i] = sn * u + cs * v;
+            }
+            na = al - t * ga;
+            nb = be + t * ga;
+            done = true;
+            rot = 1;
           }
-          __syncwarp();
-          if (lane == 0) {
-            nrm[a] = al - t * ga;
-            nrm[b] = be + t * ga;
-          }
-          rot = 1;
+        }
+        __syncwarp();              // every lane of the pair has read the old norms
+        if (done && sl == 0) {
+          nrm[a] = na;
+          nrm[b] = nb;
         }
       }
       group_sync(bar, nthr);
     }
+    // warp max of the ratios, then one atomic per warp
+    float rm32 = (float)rmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rm32 = fmaxf(rm32, __shfl_xor_sync(0xffffffffu, rm32, o));
+    const int anyrot = __any_sync(0xffffffffu, rot);
     if (lane == 0) {
-      if (rot) atomicMax(&gs.flag[g], 1);
-      atomicMax(&gs.rbits[g], __float_as_uint((float)rmax));
+      if (anyrot) atomicMax(&gs.flag[g], 1);
+      atomicMax(&gs.rbits[g], __float_as_uint(rm32));
     }
     group_sync(bar, nthr);
     const int any = gs.flag[g];
@@ -489,6 +516,31 @@ __device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, T* __restr
     if (!any || rm < stop) return sweep;
   }
   return -1;
+}
+
+// Lanes per pair from a latency model of one round: ceil(pairs / slots)
+// passes, each a fixed cost (reduction over log2 L lanes, the rotation
+// angle) plus the per-lane element work (about 3 q / L loads and FMAs).
+__device__ __forceinline__ int lanes_per_pair(int q, int p, int nw) {
+  int best = 32;
+  long long bt = -1;
+  for (int L = 32; L >= 8; L >>= 1) {
+    const int slots = nw * (32 / L);
+    const int passes = ((p + 1) / 2 + slots - 1) / slots;
+    const int lg = L == 32 ? 5 : (L == 16 ? 4 : 3);
+    const long long tcost = (long long)passes * (150 + 25 * lg + 12 * ((q + L - 1) / L));
+    if (bt < 0 || tcost < bt) bt = tcost, best = L;
+  }
+  return best;
+}
+
+template <typename T>
+__device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, T* __restrict__ V, int ldv,
+                            T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
+  const int L = lanes_per_pair(q, p, nw);
+  if (L == 8) return jacobi_lanes<T, 8>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  if (L == 16) return jacobi_lanes<T, 16>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  return jacobi_lanes<T, 32>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
 }
 
 // Warp groups for one wave of charge blocks: every block gets at least one
@@ -535,94 +587,6 @@ __device__ __forceinline__ double warp_sum64(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-// One-sided (Hestenes) Jacobi in binary64 on W (q x p column-major, q >= p,
-// leading dimension q) with the rotations accumulated into V (p x p, which
-// holds the starting basis).  Round-robin pairing, one warp per pair, the
-// column norms cached in nrm (recomputed at every sweep start).  Stops after
-// a sweep with no rotation or whose largest rotation ratio |g| / sqrt(a b)
-// is below `stop` (the next sweep's off-diagonals are then O(stop^2)).
-// Returns the sweeps used, or -1 when `max_sweeps` ran out.
-template <int NT>
-__device__ int jacobi64(double* __restrict__ W, int q, int p, double* __restrict__ V, double* __restrict__ nrm,
-                        double stop, int max_sweeps, int32_t* flag, double* rmax_sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int nwarps = NT / 32;
-  const double tol = sqrt((double)q) * 2.220446049250313e-16;
-  const int p2 = p + (p & 1);
-  for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
-    for (int j = warp; j < p; j += nwarps) {
-      const double* cj = W + (size_t)j * q;
-      double s2 = 0.0;
-      for (int i = lane; i < q; i += 32) s2 = fma(cj[i], cj[i], s2);
-      s2 = warp_sum64(s2);
-      if (lane == 0) nrm[j] = s2;
-    }
-    if (tid == 0) {
-      *flag = 0;
-      *rmax_sh = 0.0;
-    }
-    __syncthreads();
-    double rmax = 0.0;
-    int rot = 0;
-    for (int rd = 0; rd < p2 - 1; ++rd) {
-      for (int pi = warp; pi < p2 / 2; pi += nwarps) {
-        int a, b;
-        if (pi == 0) {
-          a = rd;
-          b = p2 - 1;
-        } else {
-          a = (rd + pi) % (p2 - 1);
-          b = (rd - pi + (p2 - 1)) % (p2 - 1);
-        }
-        if (a >= p || b >= p) continue;
-        double* ca = W + (size_t)a * q;
-        double* cb = W + (size_t)b * q;
-        double ga = 0.0;
-        for (int i = lane; i < q; i += 32) ga = fma(ca[i], cb[i], ga);
-        ga = warp_sum64(ga);
-        const double al = nrm[a], be = nrm[b];
-        if (ga != 0.0 && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          rmax = fmax(rmax, fabs(ga) / (sqrt(al) * sqrt(be)));
-          const double zeta = (be - al) / (2.0 * ga);
-          double t;
-          if (fabs(zeta) > 1e150) t = 0.5 / zeta;
-          else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-          for (int i = lane; i < q; i += 32) {
-            const double x = ca[i], y = cb[i];
-            ca[i] = cs * x - sn * y;
-            cb[i] = sn * x + cs * y;
-          }
-          double* va = V + (size_t)a * p;
-          double* vb = V + (size_t)b * p;
-          for (int i = lane; i < p; i += 32) {
-            const double x = va[i], y = vb[i];
-            va[i] = cs * x - sn * y;
-            vb[i] = sn * x + cs * y;
-          }
-          __syncwarp();
-          if (lane == 0) {
-            nrm[a] = al - t * ga;
-            nrm[b] = be + t * ga;
-          }
-          rot = 1;
-        }
-      }
-      __syncthreads();
-    }
-    if (lane == 0) {
-      if (rot) atomicMax(flag, 1);
-      atomicMax(reinterpret_cast<unsigned long long*>(rmax_sh), (unsigned long long)__double_as_longlong(rmax));
-    }
-    __syncthreads();
-    const int any = *flag;
-    const double rm = *rmax_sh;
-    __syncthreads();
-    if (!any || rm < stop) return sweep;
-  }
-  return -1;
 }
 
 // Truncation rule (Sec. II): smallest k >= 1 whose discarded weight

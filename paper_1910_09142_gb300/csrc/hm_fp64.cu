@@ -395,51 +395,31 @@ __device__ void two_site_op(ChainDev* c, const OpDev op, int t, Shared& sh, int3
 
 // One two-site op of a chain, block by block in the S^z charge of the new
 // middle bond (Sec. II.C): theta by block GEMMs, the gate within its
-// conserved sectors, a binary64 one-sided Jacobi per block (the blocks of a
-// split at once, each by its own warp group), then one truncation over the
-// union of the blocks' singular values (Sec. II).
+// conserved sectors, a binary64 one-sided Jacobi per block, then one
+// truncation over the union of the blocks' singular values (Sec. II).  The
+// blocks take the whole CTA in turn: the binary64 pipe (about 2 FMA per
+// clock per SM on GB300) is the bound, and every warp of the CTA is needed
+// to hide the latency of the global-memory rotations (splitting the warps
+// over the blocks of a split measured 1.7x slower).
 __device__ void two_site_op_blocked(ChainDev* c, const OpDev op, int t, Shared& sh, blk::SplitSh& ss,
-                                    blk::WaveSh& wv, blk::GroupSh& gs, int32_t* ctx_err) {
-  const int tid = threadIdx.x, warp = tid >> 5;
+                                    blk::GroupSh& gs, int32_t* ctx_err) {
   if (!blk::prepare<NT>(c, op, ss)) blk::prepare<NT>(c, op, ss);
   blk::theta_blocks<NT, TM, TN, TK, double>(c, op.k, ss, c->theta, &sh.g.a[0][0]);
   const blk::Meta* M = reinterpret_cast<const blk::Meta*>(c->meta);
   int sweeps = 0;
   int64_t cost = -1;
-  for (int b0 = 0; b0 < ss.nblk;) {
-    if (tid == 0) {
-      int p[15];
-      int n = 0;
-      while (b0 + n < ss.nblk && n < 15 && n < NT / 32) p[n] = M->b[b0 + n].p, ++n;
-      wv.b0 = b0;
-      wv.n = n;
-      blk::assign_warps(p, n, NT / 32, wv.w0, wv.nw);
-    }
+  for (int b = 0; b < ss.nblk; ++b) {
+    const blk::BlockRec& r = M->b[b];
+    blk::gather_block<NT, double, double>(c, op.k, ss, r, c->theta, c->W + r.woff, r.q, c->V + r.voff, r.p);
     __syncthreads();
-    const int n = wv.n;
-    for (int i = 0; i < n; ++i) {
-      const blk::BlockRec& r = M->b[b0 + i];
-      blk::gather_block<NT, double, double>(c, op.k, ss, r, c->theta, c->W + r.woff, r.q, c->V + r.voff, r.p);
+    const int sw = blk::jacobi_group<double>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig,
+                                             threadIdx.x >> 5, NT / 32, 1, 0, gs, 1e-9, kMaxSweeps);
+    if (sw < 0) {
+      set_error(c, HM_ERR_NUMERIC, t, ctx_err);
+      return;
     }
-    __syncthreads();
-    const int g = blk::my_group(wv, warp);
-    if (g >= 0) {
-      const blk::BlockRec& r = M->b[b0 + g];
-      const int sw = blk::jacobi_group<double>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig + r.svoff,
-                                               warp - wv.w0[g], wv.nw[g], g + 1, g, gs, 1e-9, kMaxSweeps);
-      if (warp == wv.w0[g] && (tid & 31) == 0) wv.sw[g] = sw;
-    }
-    __syncthreads();
-    for (int i = 0; i < n; ++i) {
-      if (wv.sw[i] < 0) {
-        set_error(c, HM_ERR_NUMERIC, t, ctx_err);
-        return;
-      }
-      const blk::BlockRec& r = M->b[b0 + i];
-      const int64_t cb = (int64_t)r.q * r.p * r.p;   // sweeps of the costliest block
-      if (cb > cost) cost = cb, sweeps = wv.sw[i];
-    }
-    b0 += n;
+    const int64_t cb = (int64_t)r.q * r.p * r.p;   // sweeps of the costliest block
+    if (cb > cost) cost = cb, sweeps = sw;
     __syncthreads();
   }
   blk::finish<NT>(c, op, t, ss, c->theta, ctx_err, sweeps, 0);
@@ -463,7 +443,6 @@ __device__ void two_site_op_blocked(ChainDev* c, const OpDev op, int t, Shared& 
 __global__ void __launch_bounds__(NT) evolve_fp64_kernel(BatchArg b, OutArg o) {
   __shared__ Shared sh;
   __shared__ blk::SplitSh ss;
-  __shared__ blk::WaveSh wv;
   __shared__ blk::GroupSh gs;
   ChainDev* c = b.c[blockIdx.x];
   const OpDev* ops = b.ops_override ? b.ops_override : c->ops;
@@ -472,7 +451,7 @@ __global__ void __launch_bounds__(NT) evolve_fp64_kernel(BatchArg b, OutArg o) {
   for (int t = b.t0; t < t1; ++t) {
     if (*(volatile int32_t*)c->status != 0) return;
     __syncthreads();
-    two_site_op_blocked(c, ops[t], t, sh, ss, wv, gs, o.ctx_err);
+    two_site_op_blocked(c, ops[t], t, sh, ss, gs, o.ctx_err);
     __syncthreads();
   }
 }

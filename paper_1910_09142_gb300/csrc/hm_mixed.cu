@@ -393,7 +393,8 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       for (int e = tid; e < r.q * r.p; e += NT) W64[e] = (double)W32[e];
       for (int e = tid; e < r.p * r.p; e += NT) V64[e] = (double)V32[e];
       __syncthreads();
-      const int s64 = blk::jacobi64<NT>(W64, r.q, r.p, V64, c->sig, kPolishStop, kMaxSweeps, &sc.ival[0], &sc.dval[1]);
+      const int s64 = blk::jacobi_group<double>(W64, r.q, r.q, r.p, V64, r.p, c->sig, warp, NT / 32, 1, 0, gs,
+                                                kPolishStop, kMaxSweeps);
       if (s64 < 0) {
         set_error(c, HM_ERR_NUMERIC, t, ctx_err);
         return;

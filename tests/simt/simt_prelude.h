@@ -61,6 +61,12 @@ inline T __shfl_xor_sync(unsigned, T v, int lane_mask, int = 32) {
   return out;
 }
 
+inline int __any_sync(unsigned mask, int pred) {
+  int v = pred != 0;
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
 inline long long __double_as_longlong(double d) {
   long long r;
   std::memcpy(&r, &d, sizeof r);
