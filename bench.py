@@ -36,7 +36,7 @@ METRIC = "hybrid-METTS samples/s (Lx=16 ladder, chi=256)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)    # one step is ~70 s of GPU time (256 samples)
+    ap.add_argument("--steps", type=int, default=5)    # one step is 256 samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])

@@ -209,6 +209,16 @@ int hm_collapse(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, do
 int hm_collapse_device(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out_dev,
                        double* logp_out_dev);
 
+/* Step 4 with its intermediate results, for parity checks: as hm_collapse,
+ * and cond_out (HOST, n * n_env * 3 doubles) receives, per environment site
+ * in collapse order, the conditional probabilities p(b | outcomes before it)
+ * of the three basis states of that sample's basis (Eq. detailbalance1: the
+ * probability of the drawn string is their product along the outcomes).
+ * The chains must share n_env.  env_out, logp_out and cond_out must not be
+ * NULL.  Synchronises; stages through an arena block like hm_collapse. */
+int hm_collapse_conditionals(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, double* logp_out,
+                             double* cond_out);
+
 /* Per-chain counters since init, to HOST out[HM_NUM_STATS]:
  * [0] flops of the two-site contractions, counted block by block
  *     (2 rows x inner x columns of every charge block, Sec. II.C),

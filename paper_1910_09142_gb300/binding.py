@@ -36,7 +36,7 @@ EXPORTS = ["hm_create", "hm_destroy", "hm_query_memory", "hm_num_obs", "hm_num_e
            "hm_free_chain", "hm_evolve", "hm_measure_cluster", "hm_measure_cluster_device",
            "hm_collapse", "hm_collapse_device", "hm_chain_stats", "hm_get_mps", "hm_set_mps",
            "hm_apply_ops", "hm_plan", "hm_gates", "hm_last_error", "hm_two_site_update_static",
-           "hm_measure_susceptibility", "hm_resume_chain"]
+           "hm_measure_susceptibility", "hm_resume_chain", "hm_collapse_conditionals"]
 
 
 class HmError(RuntimeError):
@@ -96,6 +96,7 @@ def load(path=None):
         "hm_measure_cluster_device": [vp, P(i64), i32, vp, i32],
         "hm_collapse": [vp, P(i64), i32, vp, vp],
         "hm_collapse_device": [vp, P(i64), i32, vp, vp],
+        "hm_collapse_conditionals": [vp, P(i64), i32, vp, vp, vp],
         "hm_chain_stats": [vp, i64, vp],
         "hm_get_mps": [vp, i64, vp, i32, vp, sz, P(i32), P(sz)],
         "hm_set_mps": [vp, i64, vp, i32, vp, sz, i32, i32],
@@ -281,6 +282,16 @@ class Context:
         logp = np.zeros(len(arr))
         self._c(self.lib.hm_collapse(self.h, ptr, len(arr), _ptr(env), _ptr(logp)))
         return env[:, :n_env], logp
+
+    def collapse_conditionals(self, ids, n_env):
+        """Collapse and reset; returns (outcomes, log p, conditional
+        probabilities of shape (len(ids), n_env, 3))."""
+        arr, ptr = _ids(ids)
+        env = np.zeros((len(arr), max(n_env, 1)), dtype=np.int8)
+        logp = np.zeros(len(arr))
+        cond = np.zeros((len(arr), max(n_env, 1), 3))
+        self._c(self.lib.hm_collapse_conditionals(self.h, ptr, len(arr), _ptr(env), _ptr(logp), _ptr(cond)))
+        return env[:, :n_env], logp, cond[:, :n_env]
 
     def collapse_device(self, ids, env_tensor=None, logp_tensor=None):
         """Collapse and reset, asynchronously; outcomes into an int8 CUDA tensor

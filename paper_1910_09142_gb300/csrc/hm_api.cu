@@ -975,13 +975,13 @@ int hm_measure_susceptibility(hm_ctx* ctx, const hm_chain* ids, int32_t n, doubl
 }
 
 static int collapse_impl(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_dev, double* logp_dev,
-                         std::vector<Chain*>& cs) {
+                         std::vector<Chain*>& cs, double* cond_dev = nullptr) {
   int rc = lookup(ctx, ids, n, &cs);
   if (rc) return rc;
   int n_env = -1;
   for (Chain* c : cs) {
     if (c->phase != 1) return fail(&ctx->err, HM_ERR_STATE, "collapse needs an evolved chain");
-    if (env_dev && n_env >= 0 && c->L.n_env != n_env)
+    if ((env_dev || cond_dev) && n_env >= 0 && c->L.n_env != n_env)
       return fail(&ctx->err, HM_ERR_ARG, "chains of one collapse call must share n_env when env_out is given");
     n_env = c->L.n_env;
   }
@@ -992,6 +992,7 @@ static int collapse_impl(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* en
   rc = for_batches(cs, [&](BatchArg& b, int s) {
     o.env = env_dev ? env_dev + (size_t)s * o.n_env : nullptr;
     o.logp = logp_dev ? logp_dev + s : nullptr;
+    o.cond = cond_dev ? cond_dev + (size_t)s * o.n_env * 3 : nullptr;
     return launch_collapse_fp64(b, o, ctx->stream);
   });
   if (rc != HM_OK) return fail(&ctx->err, rc, "collapse launch failed");
@@ -1030,6 +1031,35 @@ int hm_collapse(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, do
     HM_CUDA(ctx, cudaMemcpyAsync(env_out, env_dev, (size_t)n * n_env, cudaMemcpyDeviceToHost, ctx->stream));
   if (logp_out)
     HM_CUDA(ctx, cudaMemcpyAsync(logp_out, logp_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return check_device_error(ctx);
+}
+
+int hm_collapse_conditionals(hm_ctx* ctx, const hm_chain* ids, int32_t n, int8_t* env_out, double* logp_out,
+                             double* cond_out) {
+  Range range("hm_collapse_conditionals");
+  if (!ctx) return fail(nullptr, HM_ERR_ARG, "null context");
+  if (n == 0) return HM_OK;
+  if (!env_out || !logp_out || !cond_out) return fail(&ctx->err, HM_ERR_ARG, "null output");
+  std::vector<Chain*> cs;
+  int rc = lookup(ctx, ids, n, &cs);
+  if (rc) return rc;
+  const size_t n_env = (size_t)cs[0]->L.n_env;
+  const size_t env_bytes = align_up(std::max<size_t>((size_t)n * n_env, 1));
+  const size_t cond_bytes = align_up(std::max<size_t>((size_t)n * n_env * 3 * sizeof(double), 8));
+  Scratch sc{ctx};
+  rc = sc.get(env_bytes + cond_bytes + (size_t)n * sizeof(double));
+  if (rc) return rc;
+  int8_t* env_dev = (int8_t*)sc.ptr;
+  double* cond_dev = (double*)(sc.ptr + env_bytes);
+  double* logp_dev = (double*)(sc.ptr + env_bytes + cond_bytes);
+  rc = collapse_impl(ctx, ids, n, env_dev, logp_dev, cs, cond_dev);
+  if (rc) return rc;
+  if (n_env) {
+    HM_CUDA(ctx, cudaMemcpyAsync(env_out, env_dev, (size_t)n * n_env, cudaMemcpyDeviceToHost, ctx->stream));
+    HM_CUDA(ctx, cudaMemcpyAsync(cond_out, cond_dev, (size_t)n * n_env * 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  }
+  HM_CUDA(ctx, cudaMemcpyAsync(logp_out, logp_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_device_error(ctx);
 }
 

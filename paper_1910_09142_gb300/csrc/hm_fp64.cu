@@ -984,6 +984,8 @@ __global__ void __launch_bounds__(NT) collapse_fp64_kernel(BatchArg b, OutArg o)
         double pb = 0.0;
         if (tot > 0.0 && isfinite(tot)) {
           const double p[3] = {q[0] / tot, q[1] / tot, q[2] / tot};
+          if (o.cond)
+            for (int bb = 0; bb < 3; ++bb) o.cond[((size_t)blockIdx.x * o.n_env + e_ord) * 3 + bb] = p[bb];
           const double u = philox_uniform((uint32_t)n_sample, (uint32_t)e_ord, c->seed_hi, c->seed_lo,
                                           c->chain_id);
           pick = choose3(p, u);

@@ -98,6 +98,7 @@ struct OutArg {
   int32_t n_env;      // stride of env_out
   int8_t* env;        // device, n * n_env (collapse) or nullptr
   double* logp;       // device, n (collapse) or nullptr
+  double* cond;       // device, n * n_env * 3 conditional probabilities (collapse) or nullptr
   int32_t* ctx_err;   // device error word shared by the context
 };
 

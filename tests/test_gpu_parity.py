@@ -260,3 +260,44 @@ def test_admission_refused_without_side_effects():
     ok = small.init_chain(b.params(2, 2, chi_max=4))         # the arena is still usable
     small.free_chain(ok)
     small.close()
+
+
+def _oracle_sample_conds(ref):
+    """One oracle Markov step that also returns the collapse's conditional
+    probabilities (Eq. detailbalance1, one vector per environment site)."""
+    from oracle import collapse as ocol
+    from oracle import measure as omeas
+    st = ref.evolve()
+    obs = omeas.measure(st, ref.meas_bonds)
+    basis = ocol.sample_basis(ref.n, ref.basis_zx)
+    out, logp, conds = ocol.collapse(st, ref.ladder, basis, ref.seed, ref.chain_id, ref.n)
+    ref.env, ref.env_basis = out, basis
+    ref.n += 1
+    return obs, list(out), logp, np.array(conds, dtype=np.float64).reshape(-1, 3)
+
+
+def test_collapse_conditionals_match_oracle(ctx):
+    """Per-site conditional probabilities of the collapse (hm_collapse_conditionals)
+    at 1e-10 relative (1e-14 absolute floor), three samples (S^z, S^x, S^z
+    bases) of the chains whose state is stable under rounding."""
+    b = _b()
+    cfgs = [CFGS[0], CFGS[2], CFGS[3]]
+    ps = [b.params(**cfg, seed=13, chain_id=4) for cfg in cfgs]
+    ids = [ctx.init_chain(p) for p in ps]
+    try:
+        refs = [ochain.HybridChain(seed=13, chain_id=4, **cfg) for cfg in cfgs]
+        for _ in range(3):
+            ctx.evolve(ids)
+            for cid, p, ref in zip(ids, ps, refs):
+                n_env = b.num_env(p)
+                obs = ctx.measure([cid], b.num_obs(p))[0]
+                env, logp, cond = ctx.collapse_conditionals([cid], n_env)
+                r_obs, r_env, r_logp, r_cond = _oracle_sample_conds(ref)
+                assert np.allclose(obs, r_obs, rtol=RTOL, atol=ATOL)
+                assert list(env[0]) == r_env
+                assert cond[0].shape == r_cond.shape
+                assert np.all(np.abs(cond[0] - r_cond) <= 1e-10 * r_cond + 1e-14), np.abs(cond[0] - r_cond).max()
+                assert abs(logp[0] - r_logp) <= 1e-10 * max(1.0, abs(r_logp))
+    finally:
+        for cid in ids:
+            ctx.free_chain(cid)
