@@ -327,6 +327,31 @@ __device__ void set_error(const ChainDev* c, int code, int where, int32_t* ctx_e
   }
 }
 
+// Promotes a binary32 Jacobi result to binary64: V64 = V32 with every column
+// scaled to unit norm and W64 = W32 with the same column scales.  A binary32
+// Givens rotation with a small angle t has cs = 1 exactly once 1 + t^2 rounds
+// to 1, so it stretches both columns by sqrt(1 + t^2): a bias that never
+// cancels, and after the ~10^3 rotations a column sees it leaves V's columns
+// longer than 1 by ~1e-5.  Left in, each kept singular vector would be
+// weighted by its column's stretch, a systematic error in every sample.
+// W = theta V holds column by column, so scaling both keeps it.  One warp per
+// column; scale: p doubles of scratch.
+__device__ void promote_unit(const float* W32, int ldw, const float* V32, int ldv, int q, int p, double* W64,
+                             double* V64, double* scale) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < p; j += NT / 32) {
+    const float* v = V32 + (size_t)j * ldv;
+    double s2 = 0.0;
+    for (int i = lane; i < p; i += 32) s2 = fma((double)v[i], (double)v[i], s2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) scale[j] = s2 > 0.0 ? 1.0 / sqrt(s2) : 1.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < q * p; e += NT) W64[e] = (double)W32[(size_t)(e / q) * ldw + e % q] * scale[e / q];
+  for (int e = threadIdx.x; e < p * p; e += NT) V64[e] = (double)V32[(size_t)(e / p) * ldv + e % p] * scale[e / p];
+}
+
 // Shared memory of the binary32 block Jacobi; the kernel's dynamic shared
 // memory is at least this (and at least the staged fallback's plan).
 constexpr size_t kBlockSmem = 210 * 1024;
@@ -390,8 +415,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       }
       double* W64 = c->W + r.woff;
       double* V64 = c->V + r.voff;
-      for (int e = tid; e < r.q * r.p; e += NT) W64[e] = (double)W32[e];
-      for (int e = tid; e < r.p * r.p; e += NT) V64[e] = (double)V32[e];
+      promote_unit(W32, r.q, V32, r.p, r.q, r.p, W64, V64, c->sig);
       __syncthreads();
       const int s64 = blk::jacobi_group<double>(W64, r.q, r.q, r.p, V64, r.p, c->sig, warp, NT / 32, 1, 0, gs,
                                                 kPolishStop, kMaxSweeps);
@@ -427,8 +451,8 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       const float* V32 = W32 + (size_t)r.p * (r.q | 1);
       double* W64 = c->W + r.woff;
       double* V64 = c->V + r.voff;
-      for (int e = tid; e < r.q * r.p; e += NT) W64[e] = (double)W32[(size_t)(e / r.q) * (r.q | 1) + e % r.q];
-      for (int e = tid; e < r.p * r.p; e += NT) V64[e] = (double)V32[(size_t)(e / r.p) * (r.p | 1) + e % r.p];
+      promote_unit(W32, r.q | 1, V32, r.p | 1, r.q, r.p, W64, V64, c->sig + r.svoff);
+      __syncthreads();
     }
     __syncthreads();
     if (g >= 0) {
