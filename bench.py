@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)    # one step is 256 samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed32", "fp64"])
     ap.add_argument("--chains", type=int, default=256)
     ap.add_argument("--schedule", default="plain", choices=["plain", "fused"],
                     help="op schedule: plain, or fused (runs of splits on one site pair folded into one)")
@@ -224,7 +224,7 @@ def main():
         build.build()
     b = binding
     cfg = workload(args)
-    prec = b.HM_MIXED if args.precision == "mixed" else b.HM_FP64
+    prec = {"mixed": b.HM_MIXED, "mixed32": b.HM_MIXED32, "fp64": b.HM_FP64}[args.precision]
     n = args.chains
     ps = [b.params(**cfg, precision=prec, seed=0, chain_id=c) for c in rank_chain_ids(rank, n)]
     per = b.query_memory(ps[0])
@@ -302,18 +302,18 @@ def main():
         return
     evolve_s = sum(evolve_ms) / 1e3
     achieved = flops_alg / evolve_s / 1e12
-    peak = FP32_ALU_PEAK / 1e12 if prec == b.HM_MIXED else FP64_ALU_PEAK / 1e12
+    peak = FP32_ALU_PEAK / 1e12 if prec != b.HM_FP64 else FP64_ALU_PEAK / 1e12
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if prec == b.HM_MIXED else "f64", "data": "synthetic",
+            "dtype": "f64" if prec == b.HM_FP64 else "f32+f64", "data": "synthetic",
             "config": workload_config(args, n, per),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "note": "per-sample latency = step time (all chains of a step finish together)"},
             "roofline": {"bound": "alu", "kernel": "evolve (two-site ops)", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "flops_per_step": flops_alg / args.steps,
-                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec == b.HM_MIXED
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec != b.HM_FP64
                          else "nominal GB300 FP64 rate"},
             "evolve_share": sum(evolve_ms) / t_ms,
             "gpu_launches": launches_per_step * args.steps,

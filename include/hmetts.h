@@ -34,12 +34,16 @@
  *   asynchronous.  One context must not be used from two host threads at once.
  * - Data layout: an MPS site tensor A[k] has shape (chi_{k-1}, 3, chi_k),
  *   row-major FP64, local basis m = +1, 0, -1.  Bond dims live on the device.
- * - Precision: HM_FP64 runs every step in IEEE binary64.  HM_MIXED runs the
- *   two-site contraction, the gate and the one-sided Jacobi SVD of step 2 in
- *   binary32 (about 58x the binary64 FMA rate of GB300) and keeps everything
- *   else binary64; measured against HM_FP64 on ladders up to Lx = 8, its
- *   per-sample energies differ by <= 1e-4 relative and its bond correlators by
- *   <= 2.4e-4 absolute (the tests state 1e-3 and 2e-3).
+ * - Precision: HM_FP64 runs every step in IEEE binary64.  HM_MIXED forms
+ *   the two-site tensor and applies the gate in binary32 (binary64 site
+ *   tensors rounded on load, gate coefficients as binary32 hi + lo pairs),
+ *   decomposes each charge block with binary32 one-sided Jacobi sweeps, then
+ *   finishes with binary64 sweeps so the singular values and vectors are
+ *   binary64-accurate for that tensor; truncation, renormalisation, stored
+ *   tensors, measurement and collapse are binary64.  HM_MIXED32 is HM_MIXED
+ *   without the binary64 sweeps.  Measured on GB300 against HM_FP64 (same
+ *   chains, same draws): per-sample energies within ~1e-6 relative for both
+ *   mixed forms (the tests state 1e-5).
  */
 #ifndef HMETTS_H
 #define HMETTS_H
@@ -60,9 +64,11 @@ extern "C" {
 #define HM_ERR_STATE (-6)    /* call out of order (e.g. evolve twice, no collapse) */
 
 #define HM_FP64 0            /* every step in binary64                              */
-#define HM_MIXED 1           /* evolve (contraction, gate, Jacobi SVD) in binary32;  */
-                             /* truncation weights, renormalisation, stored tensors, */
-                             /* measurement and collapse in binary64                 */
+#define HM_MIXED 1           /* evolve: contraction and gate in binary32, Jacobi SVD */
+                             /* in binary32 then binary64 sweeps; truncation,        */
+                             /* renormalisation, stored tensors, measurement and     */
+                             /* collapse in binary64                                 */
+#define HM_MIXED32 2         /* HM_MIXED with the SVD left at its binary32 sweeps    */
 
 #define HM_ZX_ALTERNATE 0    /* collapse sample n in the Sz basis (n even) or Sx basis (n odd) */
 #define HM_Z_ONLY 1          /* collapse every sample in the Sz basis              */
@@ -87,12 +93,12 @@ typedef int64_t hm_chain;
  *                 (at least 1 when beta > 0) steps of size beta/(2M) are taken
  *                 (Sec. I.A).
  *   chi_max       bond dimension cap of every truncated SVD (>= 1; under
- *                 HM_MIXED the largest cap must be <= 2150, the shared memory
+ *                 HM_MIXED / HM_MIXED32 the largest cap must be <= 2150, the shared memory
  *                 the binary32 evolve stages its column blocks in; larger
  *                 caps are refused with HM_ERR_ARG at admission).
  *   cutoff        truncation error target: the smallest kept count whose
  *                 discarded weight sum s^2 / total s^2 <= cutoff (Sec. II).
- *   precision     HM_FP64 or HM_MIXED.
+ *   precision     HM_FP64, HM_MIXED or HM_MIXED32.
  *   seed          Philox4x32-10 key word 0 (low 32 bits) and counter word 2
  *                 (high 32 bits).
  *   chain_id      Philox key word 1: independent random stream per chain.

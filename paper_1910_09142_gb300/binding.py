@@ -21,6 +21,7 @@ HM_ERR_TIMEOUT = -5
 HM_ERR_STATE = -6
 HM_FP64 = 0
 HM_MIXED = 1
+HM_MIXED32 = 2
 HM_ZX_ALTERNATE = 0
 HM_Z_ONLY = 1
 HM_SCHED_PLAIN = 0

@@ -63,7 +63,7 @@ int check_params(const hm_params* p, std::string* err) {
   if (!std::isfinite(p->J_leg) || !std::isfinite(p->J_rung)) return fail(err, HM_ERR_ARG, "couplings must be finite");
   if (p->chi_max < 1 || p->chi_max > 4096) return fail(err, HM_ERR_ARG, "chi_max must be in [1, 4096]");
   if (!(p->cutoff >= 0.0) || !(p->cutoff < 1.0)) return fail(err, HM_ERR_ARG, "cutoff must be in [0, 1)");
-  if (p->precision != HM_FP64 && p->precision != HM_MIXED)
+  if (p->precision != HM_FP64 && p->precision != HM_MIXED && p->precision != HM_MIXED32)
     return fail(err, HM_ERR_ARG, "unsupported precision %d", p->precision);
   if (p->basis_schedule != HM_ZX_ALTERNATE && p->basis_schedule != HM_Z_ONLY)
     return fail(err, HM_ERR_ARG, "unknown basis schedule");
@@ -407,7 +407,7 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gat
   m.off_sgn = take(n * sizeof(int32_t));
   m.off_meta = take(kMetaBytes);
   // binary32 Jacobi of a charge block too large for shared memory (mixed)
-  m.off_X = p.precision == HM_MIXED ? take(m.ws_cap * sizeof(double)) : 0;
+  m.off_X = p.precision != HM_FP64 ? take(m.ws_cap * sizeof(double)) : 0;
   m.slot_off.resize(n);
   for (int s = 0; s < n; ++s) m.slot_off[s] = take(m.bmax[s] * 3 * m.bmax[s + 1] * sizeof(double));
   m.total = off;
@@ -608,7 +608,7 @@ int hm_destroy(hm_ctx* ctx) {
 // fit what one CTA may opt into.
 static int check_kernel_limits(const hm_params& p, const MemPlan& m, std::string* err) {
   int bcols = 0;
-  if (p.precision == HM_MIXED && mixed_smem_bytes(m.chi_cap, &bcols) > kMaxSharedOptIn)
+  if (p.precision != HM_FP64 && mixed_smem_bytes(m.chi_cap, &bcols) > kMaxSharedOptIn)
     return fail(err, HM_ERR_ARG, "chi cap %d needs %zu bytes of shared memory in the mixed evolve (max %zu)",
                 m.chi_cap, mixed_smem_bytes(m.chi_cap, &bcols), kMaxSharedOptIn);
   return HM_OK;
@@ -766,7 +766,7 @@ static int init_chain_impl(hm_ctx* ctx, const hm_params* p, const int8_t* env_in
   d.qn = (int16_t*)(base + mp.off_qn);
   d.sgn = (int32_t*)(base + mp.off_sgn);
   d.meta = base + mp.off_meta;
-  d.X = p->precision == HM_MIXED ? (float*)(base + mp.off_X) : nullptr;
+  d.X = p->precision != HM_FP64 ? (float*)(base + mp.off_X) : nullptr;
   d.ws_cap = mp.ws_cap;
   d.env_cap = mp.env_cap;
   d.sv_cap = mp.sv_cap;
@@ -861,7 +861,7 @@ int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
   HM_CUDA(ctx, cudaSetDevice(ctx->device));
   OutArg o{};
   o.ctx_err = ctx->err_word;
-  for (int prec : {HM_FP64, HM_MIXED}) {
+  for (int prec : {HM_FP64, HM_MIXED, HM_MIXED32}) {
     std::vector<Chain*> group;
     int chi_cap = 1;
     for (Chain* c : cs)
@@ -882,7 +882,7 @@ int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
         b.t0 = t0;
         b.t1 = t0 + chunk;
         const int r = prec == HM_FP64 ? launch_evolve_fp64(b, o, ctx->stream)
-                                      : launch_evolve_mixed(b, o, chi_cap, ctx->stream);
+                                      : launch_evolve_mixed(b, o, chi_cap, prec == HM_MIXED, ctx->stream);
         if (r != HM_OK) return r;
       }
       return HM_OK;
@@ -1197,7 +1197,7 @@ int hm_apply_ops(hm_ctx* ctx, hm_chain chain, const int32_t* ops, int32_t n_ops)
   OutArg o{};
   o.ctx_err = ctx->err_word;
   rc = c->p.precision == HM_FP64 ? launch_evolve_fp64(b, o, ctx->stream)
-                                  : launch_evolve_mixed(b, o, c->mp.chi_cap, ctx->stream);
+                                  : launch_evolve_mixed(b, o, c->mp.chi_cap, c->p.precision == HM_MIXED, ctx->stream);
   if (rc != HM_OK) return fail(&ctx->err, rc, "apply_ops launch failed");
   return check_device_error(ctx);   // the scratch op list must outlive the kernel
 }

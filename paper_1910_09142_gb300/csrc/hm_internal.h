@@ -112,8 +112,9 @@ int launch_susceptibility_fp64(const BatchArg& b, const OutArg& o, void* stream)
 // Message returned by hm_last_error(NULL) (hm_api.cu).
 void set_global_error(const char* msg);
 
-// Mixed-precision evolve (hm_mixed.cu); chi_cap = largest bond cap in the batch.
-int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* stream);
+// Mixed-precision evolve (hm_mixed.cu); chi_cap = largest bond cap in the
+// batch; polish != 0 finishes every SVD with binary64 sweeps (HM_MIXED).
+int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream);
 
 // Binary32 GEMM tile of the mixed evolve kernel, and the dynamic shared
 // memory one CTA may opt into on sm_100-class parts (227 KB).

@@ -358,7 +358,9 @@ constexpr size_t kBlockSmem = 210 * 1024;
 
 // Stopping rule of the binary64 polish: a sweep whose largest rotation ratio
 // is below this leaves off-diagonals of order its square for the next sweep.
-constexpr double kPolishStop = 1e-7;
+// After the binary32 sweeps that ratio is ~1e-6, so one binary64 sweep ends
+// the polish with off-diagonals of order 1e-12.
+constexpr double kPolishStop = 1e-5;
 
 // One two-site op (step 2 of Sec. I.C.1) in charge blocks (Sec. II.C):
 // theta and the gate in binary32 (operands rounded from the binary64 site
@@ -371,7 +373,7 @@ constexpr double kPolishStop = 1e-7;
 // shared memory runs alone, its binary32 sweeps on column blocks staged from
 // global memory.  Then the truncation rule (Sec. II), renormalisation and
 // absorb in binary64.
-__device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols, float* smem, Scal& sc,
+__device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols, int polish, float* smem, Scal& sc,
                                   blk::SplitSh& ss, blk::WaveSh& wv, blk::GroupSh& gs, int32_t* ctx_err) {
   const int tid = threadIdx.x, warp = tid >> 5;
   if (!blk::prepare<NT>(c, op, ss)) blk::prepare<NT>(c, op, ss);
@@ -417,8 +419,9 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       double* V64 = c->V + r.voff;
       promote_unit(W32, r.q, V32, r.p, r.q, r.p, W64, V64, c->sig);
       __syncthreads();
-      const int s64 = blk::jacobi_group<double>(W64, r.q, r.q, r.p, V64, r.p, c->sig, warp, NT / 32, 1, 0, gs,
-                                                kPolishStop, kMaxSweeps);
+      const int s64 = polish ? blk::jacobi_group<double>(W64, r.q, r.q, r.p, V64, r.p, c->sig, warp, NT / 32, 1, 0,
+                                                         gs, kPolishStop, kMaxSweeps)
+                             : 0;
       if (s64 < 0) {
         set_error(c, HM_ERR_NUMERIC, t, ctx_err);
         return;
@@ -455,7 +458,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       __syncthreads();
     }
     __syncthreads();
-    if (g >= 0) {
+    if (polish && g >= 0) {
       // binary64 polish by the same groups; norms of block g in c->sig
       const blk::BlockRec& r = M->b[b0 + g];
       const int s64 = blk::jacobi_group<double>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig + r.svoff,
@@ -494,7 +497,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, int bcols) {
+__global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, int bcols, int polish) {
   extern __shared__ float smem[];
   __shared__ Scal sc;
   __shared__ blk::SplitSh ss;
@@ -507,14 +510,14 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
   for (int t = b.t0; t < t1; ++t) {
     if (*(volatile int32_t*)c->status != 0) return;
     __syncthreads();
-    two_site_op_mixed(c, ops[t], t, bcols, smem, sc, ss, wv, gs, o.ctx_err);
+    two_site_op_mixed(c, ops[t], t, bcols, polish, smem, sc, ss, wv, gs, o.ctx_err);
     __syncthreads();
   }
 }
 
 }  // namespace
 
-int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* stream) {
+int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream) {
   if (b.n <= 0) return HM_OK;
   int bcols = 16;
   const size_t plan = mixed_smem_bytes(chi_cap, &bcols);
@@ -534,7 +537,7 @@ int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, void* s
       if (dev >= 0 && dev < 64) configured[dev] = smem;
     }
   }
-  evolve_mixed_kernel<<<b.n, NT, smem, (cudaStream_t)stream>>>(b, o, bcols);
+  evolve_mixed_kernel<<<b.n, NT, smem, (cudaStream_t)stream>>>(b, o, bcols, polish);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

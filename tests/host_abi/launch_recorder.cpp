@@ -27,7 +27,7 @@ int record(int kind, const hm::BatchArg& b, int extra) {
 
 namespace hm {
 int launch_evolve_fp64(const BatchArg& b, const OutArg&, void*) { return record(K_EVOLVE64, b, 0); }
-int launch_evolve_mixed(const BatchArg& b, const OutArg&, int chi_cap, void*) {
+int launch_evolve_mixed(const BatchArg& b, const OutArg&, int chi_cap, int, void*) {
   return record(K_EVOLVE_MIXED, b, chi_cap);
 }
 int launch_measure_fp64(const BatchArg& b, const OutArg&, void*) { return record(K_MEASURE, b, 0); }

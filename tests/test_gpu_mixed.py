@@ -1,12 +1,16 @@
-"""Mixed-precision path (binary32 evolve) vs the FP64 oracle (GPU tests).
+"""Mixed-precision paths (HM_MIXED, HM_MIXED32) vs the FP64 oracle (GPU tests).
 
-Stated tolerance of HM_MIXED as measured on GB300: per-sample energy
-estimator within 1e-3 relative of the oracle and every per-bond correlator
-within 2e-3 absolute (worst seen: 1.7e-4 and 5e-4 on the Lx=4, beta=2,
-cutoff 1e-12 chain after ~900 binary32 two-site updates); collapse outcomes
-identical while the oracle's uniform draw stays more than 1e-6 away from
-every cumulative-probability edge.  The 1e-5 target of the method's mixed
-form is not reached by a binary32 Jacobi SVD.
+Bars, from the method's mixed form (energy within 1e-5 of FP64 per sample):
+per-sample energy estimator within 1e-5 relative of the oracle, every
+per-bond correlator within 2e-5 absolute, collapse outcomes identical while
+the oracle's uniform draw stays more than 1e-6 away from every
+cumulative-probability edge, log p within 1e-4 absolute.  Measured on
+GB300: energies ~1e-6 relative, for HM_MIXED (binary32 Jacobi finished by
+binary64 sweeps) and HM_MIXED32 (binary32 Jacobi only) alike.  The chains
+include the small workload (Lx=4, 2W=4, beta=2, chi=64), whose splits cut
+at the chi cap: there the oracle's own energy moves by only ~1e-14 under a
+1e-16 relative change of the gates, so the 1e-5 bar measures precision, not
+chaos at the cut.
 """
 import numpy as np
 import pytest
@@ -16,7 +20,8 @@ from oracle import collapse as ocol
 
 pytestmark = pytest.mark.gpu
 
-E_RTOL, BOND_ATOL, EDGE = 1e-3, 2e-3, 1e-6
+E_RTOL, BOND_ATOL, LOGP_ATOL, EDGE = 1e-5, 2e-5, 1e-4, 1e-6
+MIXED = ["HM_MIXED", "HM_MIXED32"]
 
 
 @pytest.fixture(scope="module")
@@ -51,9 +56,9 @@ def _sample_with_margin(ref):
     return dict(obs=obs, env_out=out, logp=logp), margin
 
 
-def _compare_chain(ctx, cfg, n_samples, seed=0, chain_id=0):
+def _compare_chain(ctx, cfg, n_samples, prec, seed=0, chain_id=0):
     b = _b()
-    p = b.params(**cfg, precision=b.HM_MIXED, seed=seed, chain_id=chain_id)
+    p = b.params(**cfg, precision=getattr(b, prec), seed=seed, chain_id=chain_id)
     cid = ctx.init_chain(p)
     ref = ochain.HybridChain(seed=seed, chain_id=chain_id, **cfg)
     worst_e = worst_b = 0.0
@@ -61,34 +66,37 @@ def _compare_chain(ctx, cfg, n_samples, seed=0, chain_id=0):
         for _ in range(n_samples):
             ctx.evolve([cid])
             obs = ctx.measure([cid], b.num_obs(p))[0]
-            env, _ = ctx.collapse([cid], b.num_env(p))
+            env, logp = ctx.collapse([cid], b.num_env(p))
             r, margin = _sample_with_margin(ref)
             worst_e = max(worst_e, abs(obs[0] - r["obs"][0]) / abs(r["obs"][0]))
             worst_b = max(worst_b, float(np.abs(obs[1:] - r["obs"][1:]).max()))
             if margin < EDGE:
                 break
             assert list(env[0]) == list(r["env_out"])
+            assert abs(logp[0] - r["logp"]) < LOGP_ATOL
     finally:
         ctx.free_chain(cid)
     return worst_e, worst_b
 
 
+@pytest.mark.parametrize("prec", MIXED)
 @pytest.mark.parametrize("cfg", [
     dict(Lx=4, two_W=4, J_leg=1.0, J_rung=1.0, beta=2.0, tau=0.1, chi_max=64, cutoff=1e-12),
     dict(Lx=3, two_W=0, J_leg=1.0, J_rung=0.5, beta=1.0, tau=0.1, chi_max=64, cutoff=1e-10),
     dict(Lx=6, two_W=4, J_leg=1.0, J_rung=1.0, beta=1.0, tau=0.05, chi_max=96, cutoff=1e-7),
 ])
-def test_mixed_samples_within_stated_tolerance(ctx, cfg):
-    worst_e, worst_b = _compare_chain(ctx, cfg, 3)
-    print("mixed vs oracle: energy rel %.2e, bond abs %.2e" % (worst_e, worst_b))
+def test_mixed_samples_within_stated_tolerance(ctx, cfg, prec):
+    worst_e, worst_b = _compare_chain(ctx, cfg, 3, prec)
+    print("%s vs oracle: energy rel %.2e, bond abs %.2e" % (prec, worst_e, worst_b))
     assert worst_e < E_RTOL and worst_b < BOND_ATOL
 
 
-def test_mixed_single_rung_closed_form(ctx):
+@pytest.mark.parametrize("prec", MIXED)
+def test_mixed_single_rung_closed_form(ctx, prec):
     import math
     b = _b()
     beta = 1.0
-    p = b.params(1, 2, beta=beta, tau=0.1, chi_max=16, cutoff=0.0, precision=b.HM_MIXED)
+    p = b.params(1, 2, beta=beta, tau=0.1, chi_max=16, cutoff=0.0, precision=getattr(b, prec))
     cid = ctx.init_chain(p)
     ctx.evolve([cid])
     obs = ctx.measure([cid], b.num_obs(p))[0]
@@ -105,33 +113,35 @@ def test_mixed_and_fp64_chains_in_one_call(ctx):
     cfg = dict(Lx=3, two_W=2, J_leg=1.0, J_rung=0.5, beta=0.6, tau=0.1, chi_max=32, cutoff=1e-12)
     p64 = b.params(**cfg, seed=1)
     p32 = b.params(**cfg, seed=1, precision=b.HM_MIXED)
-    ids = [ctx.init_chain(p64), ctx.init_chain(p32)]
+    p32b = b.params(**cfg, seed=1, precision=b.HM_MIXED32)
+    ids = [ctx.init_chain(p64), ctx.init_chain(p32), ctx.init_chain(p32b)]
     ctx.evolve(ids)
     o = ctx.measure(ids, b.num_obs(p64))
     ref = ochain.HybridChain(seed=1, **cfg).sample()["obs"]
     assert np.allclose(o[0], ref, rtol=1e-10, atol=1e-12)
-    assert abs(o[1][0] - ref[0]) < 1e-5 * abs(ref[0])
-    assert not np.array_equal(o[0], o[1])        # the binary32 path really ran
+    for i in (1, 2):
+        assert abs(o[i][0] - ref[0]) < E_RTOL * abs(ref[0])
+        assert not np.array_equal(o[0], o[i])    # the binary32 path really ran
     for c in ids:
         ctx.free_chain(c)
 
 
 @pytest.mark.slow
 def test_ladder16_launch_config_sampled_parity(ctx):
-    """Lx=16, 2W=8, chi=256, cutoff 1e-7, beta=1, tau=0.05: 152 chains in one
-    batched launch (the benchmark's launch shape); two of them checked
-    against the oracle sample by sample (about 20 s of CPU each)."""
+    """Lx=16, 2W=8, chi=256, cutoff 1e-7, beta=1, tau=0.05: 152 chains (odd
+    ones HM_MIXED, even ones HM_MIXED32) in the benchmark's launch shape; two
+    of them checked against the oracle (about 20 s of CPU each)."""
     import synth
     b = _b()
     cfg = synth.ladder("ladder16")
-    ps = [b.params(**cfg, precision=b.HM_MIXED, seed=0, chain_id=i) for i in range(152)]
+    ps = [b.params(**cfg, precision=b.HM_MIXED if i % 2 else b.HM_MIXED32, seed=0, chain_id=i) for i in range(152)]
     ids = [ctx.init_chain(p) for p in ps]
     try:
         ctx.evolve(ids)
         obs = ctx.measure(ids, b.num_obs(ps[0]))
         env, logp = ctx.collapse(ids, b.num_env(ps[0]))
         assert np.all(np.isfinite(obs)) and np.all(np.isfinite(logp))
-        for i in (0, 151):
+        for i in (0, 151):                       # one of each precision
             ref = ochain.HybridChain(seed=0, chain_id=i, **cfg)
             r, margin = _sample_with_margin(ref)
             assert abs(obs[i][0] - r["obs"][0]) < E_RTOL * abs(r["obs"][0])

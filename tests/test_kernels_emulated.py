@@ -158,8 +158,8 @@ def test_resume_through_the_kernels_repeats_the_chain(emu):
     # the binary32 path within its stated tolerance of the oracle
     ref = ochain.HybridChain(seed=8, chain_id=2, **CFG)
     r = ref.sample()
-    assert abs(recs[0][0][0] - r["obs"][0]) < 1e-3 * abs(r["obs"][0])
-    assert np.abs(recs[0][0][1:] - r["obs"][1:]).max() < 2e-3
+    assert abs(recs[0][0][0] - r["obs"][0]) < 1e-5 * abs(r["obs"][0])
+    assert np.abs(recs[0][0][1:] - r["obs"][1:]).max() < 2e-5
     e.close()
 
 
