@@ -277,9 +277,9 @@ int hm_gates(const hm_params* p, double* out, int32_t cap, int32_t* n_gates_out)
 
 /* ---- Allocation-free entry point -------------------------------------------
  * The paper has no counterpart: this is a library convenience.  It serves
- * callers that cannot call cudaMalloc (work captured into a CUDA graph, code
- * running inside another framework's memory pool, processes whose device
- * allocator belongs to someone else): it performs ONE two-site update of
+ * callers that cannot call cudaMalloc (code running inside another
+ * framework's memory pool, processes whose device allocator belongs to
+ * someone else, paths that must not allocate while they run): it performs ONE two-site update of
  * step 2 -- theta = A B, the 9x9 gate, the binary64 one-sided Jacobi SVD,
  * the truncation rule and the absorb -- with all scratch in a fixed device
  * array of the library (about 4.3 MB, kept by every GPU that loads the

@@ -1166,9 +1166,9 @@ int launch_reset(const BatchArg& b, const OutArg& o, int draw_initial, void* str
 // ---------------------------------------------------------------------------
 // Allocation-free two-site update (hm_two_site_update_static).
 //
-// For callers that cannot allocate device memory: code running while a CUDA
-// graph is being captured, inside another library's memory pool, or in a
-// process whose allocator is owned by someone else.  The scratch of the
+// For callers that cannot allocate device memory: code running inside
+// another library's memory pool, in a process whose allocator is owned by
+// someone else, or on a path that must not allocate while it runs.  The scratch of the
 // update (chain descriptor, site slots, theta, Jacobi matrices, singular
 // values) lives in one file-scope device array of fixed size; every GPU that
 // loads this library holds it until the process exits.  All calls share the

@@ -1,8 +1,8 @@
 """The allocation-free two-site update, against the regular path (GPU test).
 
 hm_two_site_update_static is for callers that cannot allocate device memory
-(for example while a CUDA graph is being captured, or inside another
-framework's memory pool): its scratch is a fixed array inside the library.
+(for example code inside another framework's memory pool, or a process whose
+allocator belongs to someone else): its scratch is a fixed array inside the library.
 This test drives it through the C ABI twice in a row on the same inputs and
 compares each result with the same update done by the regular entry point
 (hm_apply_ops on a chain whose workspace lives in the caller's arena), at the
