@@ -408,8 +408,8 @@ struct GroupSh {
 // arithmetic-bound).  Stops after a sweep with no rotation or whose largest
 // ratio |g| / sqrt(a b) is below `stop` (the next sweep's off-diagonals are
 // then of order stop^2).  Returns the sweeps, or -1 when max_sweeps ran out.
-template <typename T, int L>
-__device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, T* __restrict__ V, int ldv,
+template <typename T, typename TV, int L>
+__device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
   constexpr int PPW = 32 / L;              // pairs per warp at once
   const int lane = threadIdx.x & 31;
@@ -479,12 +479,13 @@ __device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, T* __restr
               x[i] = cs * u - sn * v;
               y[i] = sn * u + cs * v;
             }
-            T* vx = V + (size_t)a * ldv;
-            T* vy = V + (size_t)b * ldv;
+            TV* vx = V + (size_t)a * ldv;
+            TV* vy = V + (size_t)b * ldv;
+            const TV cv = (TV)cs, sv = (TV)sn;
             for (int i = sl; i < p; i += L) {
-              const T u = vx[i], v = vy[i];
-              vx[i] = cs * u - sn * v;
-              vy[i] = sn * u + cs * v;
+              const TV u = vx[i], v = vy[i];
+              vx[i] = cv * u - sv * v;
+              vy[i] = sv * u + cv * v;
             }
             na = al - t * ga;
             nb = be + t * ga;
@@ -534,13 +535,16 @@ __device__ __forceinline__ int lanes_per_pair(int q, int p, int nw) {
   return best;
 }
 
-template <typename T>
-__device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, T* __restrict__ V, int ldv,
+// TV: element type of V.  A binary64 polish of a binary32 result may keep V
+// in binary32: V carries binary32 accuracy from the preconditioning sweeps
+// anyway, and the polish's rotations are tiny (angles ~1e-6).
+template <typename T, typename TV = T>
+__device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
   const int L = lanes_per_pair(q, p, nw);
-  if (L == 8) return jacobi_lanes<T, 8>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
-  if (L == 16) return jacobi_lanes<T, 16>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
-  return jacobi_lanes<T, 32>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  if (L == 8) return jacobi_lanes<T, TV, 8>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  if (L == 16) return jacobi_lanes<T, TV, 16>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  return jacobi_lanes<T, TV, 32>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
 }
 
 // Warp groups for one wave of charge blocks: every block gets at least one

@@ -327,17 +327,16 @@ __device__ void set_error(const ChainDev* c, int code, int where, int32_t* ctx_e
   }
 }
 
-// Promotes a binary32 Jacobi result to binary64: V64 = V32 with every column
-// scaled to unit norm and W64 = W32 with the same column scales.  A binary32
-// Givens rotation with a small angle t has cs = 1 exactly once 1 + t^2 rounds
-// to 1, so it stretches both columns by sqrt(1 + t^2): a bias that never
-// cancels, and after the ~10^3 rotations a column sees it leaves V's columns
-// longer than 1 by ~1e-5.  Left in, each kept singular vector would be
-// weighted by its column's stretch, a systematic error in every sample.
-// W = theta V holds column by column, so scaling both keeps it.  One warp per
-// column; scale: p doubles of scratch.
-__device__ void promote_unit(const float* W32, int ldw, const float* V32, int ldv, int q, int p, double* W64,
-                             double* V64, double* scale) {
+// Column scales 1 / |v_j| of V (binary32, leading dimension ldv) into scale.
+// A binary32 Givens rotation with a small angle t has cs = 1 exactly once
+// 1 + t^2 rounds to 1, so it stretches both columns by sqrt(1 + t^2): a bias
+// that never cancels, and after the ~10^3 rotations a column sees it leaves
+// V's columns longer than 1 by ~1e-5.  Left in, each kept singular vector
+// would be weighted by its column's stretch, a systematic energy error of
+// ~2e-5 in every sample (measured on GB300).  The rotations stay conformal,
+// and W = theta V holds column by column, so scaling a column of W and of V
+// by the same factor removes the stretch.  One warp per column.
+__device__ void column_scales(const float* V32, int ldv, int p, double* scale) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = warp; j < p; j += NT / 32) {
     const float* v = V32 + (size_t)j * ldv;
@@ -348,7 +347,23 @@ __device__ void promote_unit(const float* W32, int ldw, const float* V32, int ld
     if (lane == 0) scale[j] = s2 > 0.0 ? 1.0 / sqrt(s2) : 1.0;
   }
   __syncthreads();
+}
+
+// After the binary32 sweeps: W64 = W32 with unit-column scales, V32 scaled
+// in place to unit columns.  scale: p doubles.
+__device__ void promote_w(const float* W32, int ldw, float* V32, int ldv, int q, int p, double* W64, double* scale) {
+  column_scales(V32, ldv, p, scale);
   for (int e = threadIdx.x; e < q * p; e += NT) W64[e] = (double)W32[(size_t)(e / q) * ldw + e % q] * scale[e / q];
+  for (int e = threadIdx.x; e < p * p; e += NT) {
+    float* v = V32 + (size_t)(e / p) * ldv + e % p;
+    *v = (float)((double)*v * scale[e / p]);
+  }
+}
+
+// After the polish (if any): V64 = V32 with unit columns, W64 scaled alike.
+__device__ void promote_v(const float* V32, int ldv, int q, int p, double* W64, double* V64, double* scale) {
+  column_scales(V32, ldv, p, scale);
+  for (int e = threadIdx.x; e < q * p; e += NT) W64[e] *= scale[e / q];
   for (int e = threadIdx.x; e < p * p; e += NT) V64[e] = (double)V32[(size_t)(e / p) * ldv + e % p] * scale[e / p];
 }
 
@@ -417,11 +432,13 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       }
       double* W64 = c->W + r.woff;
       double* V64 = c->V + r.voff;
-      promote_unit(W32, r.q, V32, r.p, r.q, r.p, W64, V64, c->sig);
+      promote_w(W32, r.q, V32, r.p, r.q, r.p, W64, c->sig);
       __syncthreads();
-      const int s64 = polish ? blk::jacobi_group<double>(W64, r.q, r.q, r.p, V64, r.p, c->sig, warp, NT / 32, 1, 0,
-                                                         gs, kPolishStop, kMaxSweeps)
+      const int s64 = polish ? blk::jacobi_group<double, float>(W64, r.q, r.q, r.p, V32, r.p, c->sig, warp, NT / 32,
+                                                                1, 0, gs, kPolishStop, kMaxSweeps)
                              : 0;
+      __syncthreads();
+      promote_v(V32, r.p, r.q, r.p, W64, V64, c->sig);
       if (s64 < 0) {
         set_error(c, HM_ERR_NUMERIC, t, ctx_err);
         return;
@@ -451,21 +468,27 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
     for (int i = 0; i < n; ++i) {
       const blk::BlockRec& r = M->b[b0 + i];
       const float* W32 = smem + wv.off[i];
-      const float* V32 = W32 + (size_t)r.p * (r.q | 1);
-      double* W64 = c->W + r.woff;
-      double* V64 = c->V + r.voff;
-      promote_unit(W32, r.q | 1, V32, r.p | 1, r.q, r.p, W64, V64, c->sig + r.svoff);
+      float* V32 = smem + wv.off[i] + (size_t)r.p * (r.q | 1);
+      promote_w(W32, r.q | 1, V32, r.p | 1, r.q, r.p, c->W + r.woff, c->sig + r.svoff);
       __syncthreads();
     }
-    __syncthreads();
     if (polish && g >= 0) {
-      // binary64 polish by the same groups; norms of block g in c->sig
+      // binary64 polish by the same groups: W in binary64 (global), V stays
+      // in shared memory in binary32; norms of block g in c->sig
       const blk::BlockRec& r = M->b[b0 + g];
-      const int s64 = blk::jacobi_group<double>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig + r.svoff,
-                                                warp - wv.w0[g], wv.nw[g], g + 1, g, gs, kPolishStop, kMaxSweeps);
+      float* V32 = smem + wv.off[g] + (size_t)r.p * (r.q | 1);
+      const int s64 = blk::jacobi_group<double, float>(c->W + r.woff, r.q, r.q, r.p, V32, r.p | 1, c->sig + r.svoff,
+                                                       warp - wv.w0[g], wv.nw[g], g + 1, g, gs, kPolishStop,
+                                                       kMaxSweeps);
       if (warp == wv.w0[g] && (tid & 31) == 0) wv.sw[g] = wv.sw[g] < 0 ? -1 : (s64 < 0 ? -1 : wv.sw[g] + 1000 * s64);
     }
     __syncthreads();
+    for (int i = 0; i < n; ++i) {
+      const blk::BlockRec& r = M->b[b0 + i];
+      const float* V32 = smem + wv.off[i] + (size_t)r.p * (r.q | 1);
+      promote_v(V32, r.p | 1, r.q, r.p, c->W + r.woff, c->V + r.voff, c->sig + r.svoff);
+      __syncthreads();
+    }
     for (int i = 0; i < n; ++i) {
       const int code = wv.sw[i];
       if (code < 0) {
