@@ -185,6 +185,16 @@ int hm_free_chain(hm_ctx* ctx, hm_chain chain);
  * Asynchronous.  Requires the chain to be in its initial state. */
 int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n);
 
+/* Step 2 in slices, for schedulers that bound the work of one call (a
+ * serving tick): advances each chain's evolution by at most max_ops ops of
+ * its schedule (hm_plan), from where the previous call on it stopped.  A
+ * chain whose schedule is complete is evolved (ready for measure and
+ * collapse), exactly as after hm_evolve; done_out (HOST, n, nullable)
+ * receives 1 for those chains and 0 for the others.  The slices give the
+ * same state as one hm_evolve.  HM_ERR_STATE for an evolved chain, and
+ * hm_evolve refuses a chain whose evolution is under way.  Asynchronous. */
+int hm_evolve_partial(hm_ctx* ctx, const hm_chain* ids, int32_t n, int32_t max_ops, int32_t* done_out);
+
 /* Step 3: n_obs observables per chain into the HOST array out[n * n_obs]
  * (row i = chain ids[i]).  Synchronises.  Requires an evolved chain. */
 int hm_measure_cluster(hm_ctx* ctx, const hm_chain* ids, int32_t n, double* out, int32_t n_obs);

@@ -37,7 +37,8 @@ EXPORTS = ["hm_create", "hm_destroy", "hm_query_memory", "hm_num_obs", "hm_num_e
            "hm_free_chain", "hm_evolve", "hm_measure_cluster", "hm_measure_cluster_device",
            "hm_collapse", "hm_collapse_device", "hm_chain_stats", "hm_get_mps", "hm_set_mps",
            "hm_apply_ops", "hm_plan", "hm_gates", "hm_last_error", "hm_two_site_update_static",
-           "hm_measure_susceptibility", "hm_resume_chain", "hm_collapse_conditionals"]
+           "hm_measure_susceptibility", "hm_resume_chain", "hm_collapse_conditionals",
+           "hm_evolve_partial"]
 
 
 class HmError(RuntimeError):
@@ -98,6 +99,7 @@ def load(path=None):
         "hm_collapse": [vp, P(i64), i32, vp, vp],
         "hm_collapse_device": [vp, P(i64), i32, vp, vp],
         "hm_collapse_conditionals": [vp, P(i64), i32, vp, vp, vp],
+        "hm_evolve_partial": [vp, P(i64), i32, i32, vp],
         "hm_chain_stats": [vp, i64, vp],
         "hm_get_mps": [vp, i64, vp, i32, vp, sz, P(i32), P(sz)],
         "hm_set_mps": [vp, i64, vp, i32, vp, sz, i32, i32],
@@ -255,6 +257,14 @@ class Context:
     def evolve(self, ids):
         arr, ptr = _ids(ids)
         self._c(self.lib.hm_evolve(self.h, ptr, len(arr)))
+
+    def evolve_partial(self, ids, max_ops):
+        """Advance each chain's evolution by <= max_ops ops; returns a bool
+        array: True where the chain is now evolved."""
+        arr, ptr = _ids(ids)
+        done = np.zeros(len(arr), dtype=np.int32)
+        self._c(self.lib.hm_evolve_partial(self.h, ptr, len(arr), int(max_ops), _ptr(done)))
+        return done.astype(bool)
 
     def measure(self, ids, n_obs):
         arr, ptr = _ids(ids)

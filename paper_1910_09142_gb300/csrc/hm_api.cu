@@ -394,7 +394,7 @@ MemPlan mem_plan(const hm_params& p, const Layout& L, size_t n_ops, size_t n_gat
   m.off_siteptr = take(n * sizeof(double*));
   m.off_chi = take((n + 1) * sizeof(int32_t));
   m.off_env = take(std::max(L.n_env, 1) * sizeof(int32_t));
-  m.off_cnt = take(4 * sizeof(int32_t));
+  m.off_cnt = take(8 * sizeof(int32_t));
   m.off_stats = take(ST_N * sizeof(double));
   m.off_status = take(2 * sizeof(int32_t));
   m.off_theta = take(m.ws_cap * sizeof(double));
@@ -473,6 +473,7 @@ struct Chain {
   size_t off = 0;
   ChainDev* dev = nullptr;          // device address of the descriptor
   int phase = 0;                    // 0 initial state, 1 evolved
+  int cursor = 0;                   // ops done by hm_evolve_partial (mirror of counters[4])
   int n_obs = 0;
 };
 
@@ -851,14 +852,10 @@ int hm_free_chain(hm_ctx* ctx, hm_chain chain) {
   return HM_OK;
 }
 
-int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
-  Range range("hm_evolve");
-  std::vector<Chain*> cs;
-  int rc = lookup(ctx, ids, n, &cs);
-  if (rc) return rc;
-  for (Chain* c : cs)
-    if (c->phase != 0) return fail(&ctx->err, HM_ERR_STATE, "hm_evolve needs a chain in its initial state");
-  HM_CUDA(ctx, cudaSetDevice(ctx->device));
+// Evolve launches of a chain list: one group per precision, costliest chains
+// first, batches of <= kMaxBatch; budget 0 runs whole op lists (in chunks of
+// 4096 ops), budget > 0 advances every chain's own cursor by <= budget ops.
+static int evolve_launches(hm_ctx* ctx, const std::vector<Chain*>& cs, int budget) {
   OutArg o{};
   o.ctx_err = ctx->err_word;
   for (int prec : {HM_FP64, HM_MIXED, HM_MIXED32}) {
@@ -874,21 +871,66 @@ int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
     // first), and each launch of <= kMaxBatch chains holds similar costs.
     // Equal costs keep the caller's order.
     std::stable_sort(group.begin(), group.end(), [](const Chain* a, const Chain* b) { return a->cost > b->cost; });
-    rc = for_batches(group, [&](BatchArg& b, int s) {
+    const int rc = for_batches(group, [&](BatchArg& b, int s) {
+      auto launch = [&]() {
+        return prec == HM_FP64 ? launch_evolve_fp64(b, o, ctx->stream)
+                               : launch_evolve_mixed(b, o, chi_cap, prec == HM_MIXED, ctx->stream);
+      };
+      if (budget > 0) {
+        b.budget = budget;
+        return launch();
+      }
       const int chunk = 4096;
       int batch_ops = 0;                          // this launch's longest op list
       for (int i = 0; i < b.n; ++i) batch_ops = std::max<int>(batch_ops, (int)group[s + i]->ops.size());
       for (int t0 = 0; t0 < batch_ops; t0 += chunk) {
         b.t0 = t0;
         b.t1 = t0 + chunk;
-        const int r = prec == HM_FP64 ? launch_evolve_fp64(b, o, ctx->stream)
-                                      : launch_evolve_mixed(b, o, chi_cap, prec == HM_MIXED, ctx->stream);
+        const int r = launch();
         if (r != HM_OK) return r;
       }
       return HM_OK;
     });
     if (rc != HM_OK) return fail(&ctx->err, rc, "evolve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   }
+  return HM_OK;
+}
+
+int hm_evolve_partial(hm_ctx* ctx, const hm_chain* ids, int32_t n, int32_t max_ops, int32_t* done_out) {
+  Range range("hm_evolve_partial");
+  std::vector<Chain*> cs;
+  int rc = lookup(ctx, ids, n, &cs);
+  if (rc) return rc;
+  if (max_ops < 1) return fail(&ctx->err, HM_ERR_ARG, "max_ops must be >= 1");
+  for (Chain* c : cs)
+    if (c->phase != 0) return fail(&ctx->err, HM_ERR_STATE, "hm_evolve_partial needs a chain that is not yet evolved");
+  HM_CUDA(ctx, cudaSetDevice(ctx->device));
+  rc = evolve_launches(ctx, cs, max_ops);
+  if (rc) return rc;
+  for (int32_t i = 0; i < n; ++i) {
+    Chain* c = cs[i];
+    c->cursor = std::min<int>(c->cursor + max_ops, (int)c->ops.size());
+    const int done = c->cursor >= (int)c->ops.size();
+    if (done) {
+      c->phase = 1;
+      c->cursor = 0;
+    }
+    if (done_out) done_out[i] = done;
+  }
+  return HM_OK;
+}
+
+int hm_evolve(hm_ctx* ctx, const hm_chain* ids, int32_t n) {
+  Range range("hm_evolve");
+  std::vector<Chain*> cs;
+  int rc = lookup(ctx, ids, n, &cs);
+  if (rc) return rc;
+  for (Chain* c : cs)
+    if (c->phase != 0 || c->cursor != 0)
+      return fail(&ctx->err, HM_ERR_STATE, "hm_evolve needs a chain in its initial state");
+  HM_CUDA(ctx, cudaSetDevice(ctx->device));
+  rc = evolve_launches(ctx, cs, 0);
+  if (rc) return rc;
   for (Chain* c : cs) c->phase = 1;
   return HM_OK;
 }
@@ -1154,10 +1196,12 @@ int hm_set_mps(hm_ctx* ctx, hm_chain chain, const int32_t* dims, int32_t n_sites
   // the state is stored as given (frame 0) and carries no charge labels:
   // the chain evolves in dense mode (one block per split) until its next
   // collapse resets it to a charge-labelled initial state
-  int32_t cnt[4];
+  int32_t cnt[8];
   HM_CUDA(ctx, cudaMemcpy(cnt, base + c->mp.off_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
   cnt[2] = 0;
   cnt[3] = 1;
+  cnt[4] = 0;
+  c->cursor = 0;
   HM_CUDA(ctx, cudaMemcpy(base + c->mp.off_cnt, cnt, sizeof cnt, cudaMemcpyHostToDevice));
   const std::vector<int16_t> q0((size_t)(n + 1) * c->mp.chi_cap, 0);
   const std::vector<int32_t> s0(n, 0);

@@ -61,7 +61,8 @@ struct ChainDev {
   int32_t* env_out;          // n_env: basis index of the current environment state
   int32_t* counters;         // [0] sample index n, [1] basis of the current initial state,
                              // [2] frame of the stored state (0: as is, 1: every leg rotated by R,
-                             //     which exchanges S^x and S^z), [3] dense mode (no charge labels)
+                             //     which exchanges S^x and S^z), [3] dense mode (no charge labels),
+                             // [4] op cursor of a partial evolution (hm_evolve_partial)
   double* stats;             // ST_N
   int32_t* status;           // 0 = ok, else a negative HM_ERR_* code
   int32_t* err_where;        // op index / site where the error happened
@@ -88,6 +89,8 @@ struct BatchArg {
   int32_t n;
   int32_t t0, t1;                // op range [t0, t1) for the evolve kernel
   int32_t n_override;            // op count of ops_override
+  int32_t budget;                // > 0: each chain runs ops [cursor, cursor + budget) of its own
+                                 // list from its counters[4] and advances it (t0, t1 unused)
   const OpDev* ops_override;     // explicit op list (debug / kernel parity) or nullptr
   ChainDev* c[kMaxBatch];
 };

@@ -529,8 +529,11 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
   ChainDev* c = b.c[blockIdx.x];
   const OpDev* ops = b.ops_override ? b.ops_override : c->ops;
   const int n_ops = b.ops_override ? b.n_override : c->n_ops;
-  const int t1 = b.t1 < n_ops ? b.t1 : n_ops;
-  for (int t = b.t0; t < t1; ++t) {
+  const int t0 = b.budget > 0 ? c->counters[4] : b.t0;
+  const int t1 = b.budget > 0 ? min(t0 + b.budget, n_ops) : (b.t1 < n_ops ? b.t1 : n_ops);
+  __syncthreads();                                           // every thread has read the cursor
+  if (b.budget > 0 && threadIdx.x == 0) c->counters[4] = t1;
+  for (int t = t0; t < t1; ++t) {
     if (*(volatile int32_t*)c->status != 0) return;
     __syncthreads();
     two_site_op_mixed(c, ops[t], t, bcols, polish, smem, sc, ss, wv, gs, o.ctx_err);

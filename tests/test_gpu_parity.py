@@ -301,3 +301,34 @@ def test_collapse_conditionals_match_oracle(ctx):
     finally:
         for cid in ids:
             ctx.free_chain(cid)
+
+
+@pytest.mark.parametrize("prec", ["HM_FP64", "HM_MIXED", "HM_MIXED32"])
+def test_dense_mode_after_set_mps_matches_oracle(ctx, prec):
+    """hm_set_mps drops the charge labels: the chain evolves with one block
+    per split (the unblocked SVD).  At chi = 96 those blocks reach 192 columns,
+    more than the binary32 kernel keeps in shared memory, so the mixed paths
+    take their staged global-memory Jacobi.  Sample 0 must match the oracle
+    (1e-10 FP64, 1e-5 mixed); the collapse then resets the chain to labelled
+    blocks, and sample 1 must match too."""
+    b = _b()
+    cfg = dict(Lx=3, two_W=2, J_leg=1.0, J_rung=0.5, beta=0.6, tau=0.1, chi_max=96, cutoff=1e-12)
+    p = b.params(**cfg, seed=9, chain_id=2, precision=getattr(b, prec))
+    cid = ctx.init_chain(p)
+    rtol = RTOL if prec == "HM_FP64" else 1e-5
+    atol = ATOL if prec == "HM_FP64" else 2e-5
+    try:
+        ctx.set_mps(cid, ctx.get_mps(cid))
+        ref = ochain.HybridChain(seed=9, chain_id=2, **cfg)
+        for _ in range(2):
+            ctx.evolve([cid])
+            obs = ctx.measure([cid], b.num_obs(p))[0]
+            env, _ = ctx.collapse([cid], b.num_env(p))
+            r = ref.sample()
+            assert np.abs(obs - r["obs"]).max() <= rtol * np.abs(r["obs"]).max() + atol, (obs, r["obs"])
+            assert list(env[0]) == r["env_out"]
+        st = np.zeros(b.HM_NUM_STATS)
+        st[:] = ctx.stats(cid)
+        assert st[5] > 64                      # the bond grew past the shared-memory block size
+    finally:
+        ctx.free_chain(cid)

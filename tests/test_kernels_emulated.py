@@ -46,6 +46,7 @@ def emu(tmp_path_factory):
            "hm_free_chain": [vp, i64], "hm_evolve": [vp, P(i64), i32],
            "hm_measure_cluster": [vp, P(i64), i32, vp, i32], "hm_collapse": [vp, P(i64), i32, vp, vp],
            "hm_measure_susceptibility": [vp, P(i64), i32, vp],
+           "hm_evolve_partial": [vp, P(i64), i32, i32, vp],
            "hm_get_mps": [vp, i64, P(i32), i32, vp, ctypes.c_size_t, P(i32), P(ctypes.c_size_t)],
            "hm_last_error": [vp]}
     for name, args in sig.items():
@@ -263,3 +264,31 @@ def test_allocation_free_update_matches_the_oracle_split(emu):
         assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
         iso = oB[: k * 3 * chi_r].reshape(k, -1) if absorb == model.ABSORB_L else oA[: chi_l * 3 * k].reshape(-1, k).T
         assert np.abs(iso @ iso.T - np.eye(k)).max() < 1e-12
+
+
+def test_partial_evolution_equals_one_evolve(emu):
+    """hm_evolve_partial in slices of 7 ops reaches the state of one hm_evolve
+    bit for bit (binary64 and binary32 paths), reports completion only on the
+    last slice, and leaves the chain ready for measure and collapse."""
+    for precision in (binding.HM_FP64, binding.HM_MIXED):
+        e = Emu(emu)
+        p = binding.params(**CFG, seed=12, chain_id=5, precision=precision)
+        whole, sliced = e.init(p), e.init(p)
+        e.evolve(whole)
+        n_ops = len(binding.plan(p))
+        done = np.zeros(1, dtype=np.int32)
+        ids = np.array([sliced], dtype=np.int64)
+        calls = 0
+        while True:
+            e._ok(emu.hm_evolve_partial(e.h, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1, 7,
+                                        done.ctypes.data_as(ctypes.c_void_p)))
+            calls += 1
+            if done[0]:
+                break
+            assert calls < n_ops
+        assert calls == (n_ops + 6) // 7
+        a, b = e.mps(whole), e.mps(sliced)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+        assert np.array_equal(e.measure(whole, p), e.measure(sliced, p))
+        assert e.collapse(whole, p) == e.collapse(sliced, p)
+        e.close()
