@@ -14,9 +14,16 @@ same alone and in the mix: bit-identical in binary64, and within the stated
 tolerance in the mixed-precision mode, whose column-block size follows the
 largest bond cap in the batch.
 
+With ``tick_ops`` set, a tick advances every resident chain's evolution by
+at most that many two-site ops (``hm_evolve_partial``) and measures and
+collapses only the chains whose evolution completed in it, so a long chain
+(large Lx, beta or chi) takes several ticks and no longer holds every other
+job's latency; the slices give the same samples as whole evolutions.
+
 All arithmetic of a step runs in ``libhmetts.so``; this module only
-schedules.  Latency of a sample = wall time of the tick that produced it;
-a job's queueing delay is reported separately.
+schedules.  Latency of a sample = wall time from the tick its evolution
+started to the end of the tick that produced it (one tick without
+``tick_ops``); a job's queueing delay is reported separately.
 """
 import collections
 import time
@@ -47,6 +54,7 @@ class Job:
         self.bin_size = int(bin_size)
         self.estimator = None                # Estimator over the kept samples
         self.resume_from = None              # (outcomes, sample index) of a checkpoint
+        self.sample_t0 = None                # start of the sample now being evolved
 
     def estimate(self):
         """Mean of every observable over the kept samples, and its binned
@@ -80,8 +88,9 @@ class Server:
     """FIFO admission by arena bytes and batch slots; one batched step per tick."""
 
     def __init__(self, ctx, arena_bytes, max_chains=448, clock=time.perf_counter,
-                 query_memory=None, num_obs=None, num_env=None, sleep=time.sleep):
+                 query_memory=None, num_obs=None, num_env=None, sleep=time.sleep, tick_ops=None):
         self.ctx = ctx
+        self.tick_ops = int(tick_ops) if tick_ops else None
         self.capacity = int(arena_bytes)
         self.max_chains = int(max_chains)
         self.clock = clock
@@ -173,29 +182,40 @@ class Server:
             return 0
         t0 = self.clock()
         ids = [j.chain for j in self.active]
-        self.ctx.evolve(ids)
+        for j in self.active:
+            if j.sample_t0 is None:
+                j.sample_t0 = t0
+        if self.tick_ops:
+            done = self.ctx.evolve_partial(ids, self.tick_ops)
+            ready = [j for j, d in zip(self.active, done) if d]
+        else:
+            self.ctx.evolve(ids)
+            ready = list(self.active)
         obs = {}
-        for n_obs, group in self._groups(self.num_obs).items():
+        for n_obs, group in self._groups(self.num_obs, ready).items():
             vals = self.ctx.measure([j.chain for j in group], n_obs)
             for j, v in zip(group, vals):
                 obs[j.id] = v
-        for n_env, group in self._groups(self.num_env).items():
+        for n_env, group in self._groups(self.num_env, ready).items():
             env, _ = self.ctx.collapse([j.chain for j in group], n_env)
             for j, e in zip(group, env):
                 j.env.append(np.array(e))
         t1 = self.clock()
-        dt = t1 - t0
-        self.busy_s += dt
+        self.busy_s += t1 - t0
         self.ticks += 1
         still = []
         for j in self.active:
+            if j.id not in obs:
+                still.append(j)                        # evolution continues next tick
+                continue
             if j.done_steps >= j.n_warmup:
                 j.results.append(obs[j.id])
                 if j.estimator is None:
                     j.estimator = Estimator(len(obs[j.id]), j.bin_size)
                 j.estimator.add(j.id, obs[j.id])
-                j.latencies.append(dt)
+                j.latencies.append(t1 - j.sample_t0)
                 self.samples += 1
+            j.sample_t0 = None
             j.done_steps += 1
             if j.complete:
                 self.ctx.free_chain(j.chain)
@@ -207,9 +227,9 @@ class Server:
         self.active = still
         return len(ids)
 
-    def _groups(self, count):
+    def _groups(self, count, jobs=None):
         groups = collections.OrderedDict()
-        for j in self.active:
+        for j in self.active if jobs is None else jobs:
             groups.setdefault(count(j.params), []).append(j)
         return groups
 

@@ -32,11 +32,24 @@ class FakeCtx:
     def evolve(self, ids):
         self.calls.append(("evolve", tuple(ids)))
 
+    def evolve_partial(self, ids, max_ops):
+        """Each chain needs Lx * 10 ops per sample (a stand-in schedule length)."""
+        self.calls.append(("evolve_partial", tuple(ids)))
+        done = []
+        for c in ids:
+            p = self.chains[c][0]
+            cur = self.chains[c][2] if len(self.chains[c]) > 2 else 0
+            cur = min(cur + max_ops, 10 * p.Lx)
+            fin = cur >= 10 * p.Lx
+            self.chains[c][2:] = [0 if fin else cur]
+            done.append(fin)
+        return np.array(done)
+
     def measure(self, ids, n_obs):
         self.calls.append(("measure", tuple(ids)))
         out = []
         for c in ids:
-            p, step = self.chains[c]
+            p, step = self.chains[c][:2]
             out.append(np.full(n_obs, 1000.0 * p.Lx + 10.0 * p.chain_id + step))
         return np.array(out)
 
@@ -306,3 +319,21 @@ def test_checkpoint_of_a_resumed_job_before_its_next_step():
     third.run()
     srv.run()
     assert all(np.array_equal(x, y) for x, y in zip(last.results, job.results)) and len(last.results) == 5
+
+
+def test_tick_op_budget_keeps_short_jobs_moving():
+    """With tick_ops, a long chain (Lx=16: 160 stand-in ops) takes several
+    ticks per sample while a short one (Lx=2: 20 ops) finishes a sample every
+    tick; each job's results equal those of whole-evolution serving."""
+    whole = serve.Server(FakeCtx(), 1 << 40)
+    sliced = serve.Server(FakeCtx(), 1 << 40, tick_ops=40)
+    for srv in (whole, sliced):
+        srv.submit(_p(16, 1), 3)
+        srv.submit(_p(2, 2), 3)
+        srv.run()
+    for a, b in zip(sorted(whole.finished, key=lambda j: j.id), sorted(sliced.finished, key=lambda j: j.id)):
+        assert [list(r) for r in a.results] == [list(r) for r in b.results]
+    long_job, short_job = sorted(sliced.finished, key=lambda j: j.id)
+    assert short_job.finished is not None and long_job.finished is not None
+    assert sliced.ticks == 12                  # 3 samples x 4 ticks of 40 ops for the long chain
+    assert len(short_job.results) == 3
