@@ -50,6 +50,15 @@ def parse():
     ap.add_argument("--two-W", type=int, default=None)
     ap.add_argument("--beta", type=float, default=None)
     ap.add_argument("--chi-max", type=int, default=None)
+    ap.add_argument("--mode", default="step", choices=["step", "serve"],
+                    help="step: the headline batched Markov steps; serve: a timed Poisson request stream "
+                         "through the continuous-batching server (its own JSON line)")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="requests per second (serve mode)")
+    ap.add_argument("--serve-duration", type=float, default=30.0, help="arrival window, s (serve mode)")
+    ap.add_argument("--serve-horizon", type=float, default=120.0, help="stop serving after, s (serve mode)")
+    ap.add_argument("--serve-samples", type=float, default=0.01,
+                    help="scale of each request's 100-2000 samples (serve mode)")
+    ap.add_argument("--tick-ops", type=int, default=512, help="two-site ops per chain per tick (serve mode)")
     ap.add_argument("--susceptibility", action="store_true",
                     help="after the run, time hm_measure_susceptibility on freshly evolved chains")
     return ap.parse_args()
@@ -204,10 +213,54 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """The serving form on one GPU: requests drawn like the fifth workload
+    (Lx in {8, 16, 32}, 2W in {4, 8}, beta log-uniform in [0.5, 16], chi in
+    {128, 256, 512}, 100-2000 samples scaled by --serve-samples) arrive as a
+    Poisson stream; the server admits them by arena bytes, advances every
+    resident chain by <= --tick-ops two-site ops per tick and reports served
+    samples/s and per-sample latency.  One JSON line, not the headline."""
+    import torch
+    from paper_1910_09142_gb300 import binding as b, build, serve
+    if not os.path.exists(build.LIB):
+        build.build()
+    torch.cuda.set_device(0)
+    prec = {"mixed": b.HM_MIXED, "mixed32": b.HM_MIXED32, "fp64": b.HM_FP64}[args.precision]
+    reqs = synth.poisson_requests(args.serve_rate, args.serve_duration, seed=0)
+    free, _ = torch.cuda.mem_get_info(0)
+    arena = int(min(free * 0.8, 180e9))
+    stream = torch.cuda.Stream(0)
+    ctx = b.Context(arena, device=0, stream=stream)
+    srv = serve.Server(ctx, arena, tick_ops=args.tick_ops)
+    stream_reqs = []
+    for i, (t, cfg, n) in enumerate(reqs):
+        n = max(1, int(round(n * args.serve_samples)))
+        stream_reqs.append((t, b.params(**cfg, precision=prec, seed=1, chain_id=i, susceptibility=False), n, 0))
+    t0 = time.perf_counter()
+    st = srv.run_stream(stream_reqs, horizon_s=args.serve_horizon)
+    wall = time.perf_counter() - t0
+    line = {"metric": "served hybrid-METTS samples/s and per-sample latency (Poisson stream)", "mode": "serve",
+            "value": st["samples"] / wall if wall > 0 else None, "unit": "samples/s",
+            "latency_p50_s": st["latency_p50_s"], "latency_p99_s": st["latency_p99_s"],
+            "queue_wait_p50_s": st["queue_wait_p50_s"], "queue_wait_p99_s": st["queue_wait_p99_s"],
+            "samples": st["samples"], "ticks": st["ticks"], "busy_s": st["busy_s"], "wall_s": wall,
+            "requests": len(stream_reqs), "jobs_finished": st["jobs_finished"],
+            "jobs_resident": st["jobs_resident"], "jobs_queued": st["jobs_queued"],
+            "config": {"rate_per_s": args.serve_rate, "arrival_window_s": args.serve_duration,
+                       "horizon_s": args.serve_horizon, "samples_scale": args.serve_samples,
+                       "tick_ops": args.tick_ops, "precision": args.precision, "arena_gb": arena / 1e9,
+                       "mix": {k: v for k, v in synth.SERVE_MIX.items()}},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "serve":
+        return run_serve(args)
     import numpy as np
     import torch
     import torch.distributed as dist
