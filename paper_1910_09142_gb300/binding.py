@@ -258,6 +258,10 @@ class Context:
         arr, ptr = _ids(ids)
         self._c(self.lib.hm_evolve(self.h, ptr, len(arr)))
 
+    def synchronize(self):
+        """Wait for every call issued on the context's stream."""
+        self.stream.synchronize()
+
     def evolve_partial(self, ids, max_ops):
         """Advance each chain's evolution by <= max_ops ops; returns a bool
         array: True where the chain is now evolved."""

@@ -188,6 +188,11 @@ class Server:
         if self.tick_ops:
             done = self.ctx.evolve_partial(ids, self.tick_ops)
             ready = [j for j, d in zip(self.active, done) if d]
+            # the slices are asynchronous: wait for them, so that a tick lasts
+            # its device time and the next tick's admission sees the clock
+            sync = getattr(self.ctx, "synchronize", None)
+            if sync is not None:
+                sync()
         else:
             self.ctx.evolve(ids)
             ready = list(self.active)
