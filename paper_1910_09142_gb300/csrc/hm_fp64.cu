@@ -8,9 +8,14 @@
 // bandwidth: a batch of >= 152 chains fills the chip.
 //
 // Steps (Sec. I.C.1): evolve (step 2) = theta GEMM + 9x9 gate + one-sided
-// Jacobi SVD + truncation (Sec. II) + absorb; measure (step 3) = transfer
-// matrices with S^z / S^+ / S^- insertions (Eq. H); collapse + reset (step 4,
-// Eq. detailbalance1, Bell pairs of Sec. I.C).
+// Jacobi SVD + truncation (Sec. II) + absorb, all in S^z charge blocks
+// (Sec. II.C, hm_block.cuh); measure (step 3) = transfer matrices with S^z /
+// S^+ / S^- insertions (Eq. H), contracted by charge block; collapse + reset
+// (step 4, Eq. detailbalance1, Bell pairs of Sec. I.C), the reset writing the
+// next initial state with its charges.  An S^x-basis sample is stored with
+// every leg rotated by R (rows: the S^x eigenvectors), which exchanges S^x
+// and S^z and leaves the gates and the Bell pairs unchanged, so it is blocked
+// too; counters[2] records that frame for the measurement and the collapse.
 #include <cuda_runtime.h>
 
 #include <cmath>

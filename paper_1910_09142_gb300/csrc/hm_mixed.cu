@@ -1,17 +1,20 @@
 // Mixed-precision evolve (step 2 of Sec. I.C.1) for GB300.
 //
 // GB300 runs binary32 FMA about 58x faster than binary64 (measured 69.9 vs
-// 1.2 TFLOP/s on 152 SMs), so this path performs the two-site contraction,
-// the 9x9 gate and the one-sided Jacobi SVD in binary32, while the
-// truncation weights (Sec. II), the renormalisation of the kept singular
-// values and the stored site tensors stay binary64.  Measurement and
-// collapse (steps 3-4) are the binary64 kernels of hm_fp64.cu.
+// 1.2 TFLOP/s on 152 SMs), so this path forms the two-site tensor and applies
+// the 9x9 gate in binary32 and runs the one-sided Jacobi sweeps of every
+// charge block (Sec. II.C, hm_block.cuh) in binary32.  HM_MIXED then finishes
+// each block with one binary64 sweep (the singular values and left vectors
+// become binary64-accurate for that tensor); HM_MIXED32 stops at the binary32
+// sweeps.  The truncation weights (Sec. II), the renormalisation of the kept
+// singular values and the stored site tensors stay binary64.  Measurement
+// and collapse (steps 3-4) are the binary64 kernels of hm_fp64.cu.
 //
-// One CTA owns one chain.  The Jacobi keeps W (q x p) and V (p x p) in the
-// chain's global workspace and works on pairs of column blocks staged in
-// shared memory: intra-block pairs once per sweep, then every cross pair of
-// two blocks while both blocks sit in shared memory, so each staged column
-// is reused by b rotations.
+// One CTA owns one chain.  The blocks of a split that fit in shared memory
+// together form a wave and are decomposed at once, each by its own warp
+// group; a block too large for shared memory keeps W and V in global memory
+// and works on pairs of column blocks staged in shared memory (intra-block
+// pairs once per sweep, then every cross pair of two staged blocks).
 #include <cuda_runtime.h>
 
 #include <cfloat>
