@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--serve-samples", type=float, default=0.01,
                     help="scale of each request's 100-2000 samples (serve mode)")
     ap.add_argument("--tick-ops", type=int, default=512, help="two-site ops per chain per tick (serve mode)")
+    ap.add_argument("--serve-chains", type=int, default=4,
+                    help="independent chains a request's samples are spread over (serve mode)")
     ap.add_argument("--susceptibility", action="store_true",
                     help="after the run, time hm_measure_susceptibility on freshly evolved chains")
     return ap.parse_args()
@@ -218,7 +220,8 @@ def run_serve(args):
     (Lx in {8, 16, 32}, 2W in {4, 8}, beta log-uniform in [0.5, 16], chi in
     {128, 256, 512}, 100-2000 samples scaled by --serve-samples) arrive as a
     Poisson stream; the server admits them by arena bytes, advances every
-    resident chain by <= --tick-ops two-site ops per tick and reports served
+    resident chain by <= --tick-ops two-site ops per tick (a request's
+    samples spread over --serve-chains chains) and reports served
     samples/s and per-sample latency.  One JSON line, not the headline."""
     import torch
     from paper_1910_09142_gb300 import binding as b, build, serve
@@ -231,7 +234,7 @@ def run_serve(args):
     arena = int(min(free * 0.8, 180e9))
     stream = torch.cuda.Stream(0)
     ctx = b.Context(arena, device=0, stream=stream)
-    srv = serve.Server(ctx, arena, tick_ops=args.tick_ops)
+    srv = serve.Server(ctx, arena, tick_ops=args.tick_ops, chains_per_job=args.serve_chains)
     stream_reqs = []
     for i, (t, cfg, n) in enumerate(reqs):
         n = max(1, int(round(n * args.serve_samples)))
@@ -245,10 +248,12 @@ def run_serve(args):
             "queue_wait_p50_s": st["queue_wait_p50_s"], "queue_wait_p99_s": st["queue_wait_p99_s"],
             "samples": st["samples"], "ticks": st["ticks"], "busy_s": st["busy_s"], "wall_s": wall,
             "requests": len(stream_reqs), "jobs_finished": st["jobs_finished"],
-            "jobs_resident": st["jobs_resident"], "jobs_queued": st["jobs_queued"],
+            "jobs_resident": st["jobs_resident"], "chains_resident": st["chains_resident"],
+            "jobs_queued": st["jobs_queued"],
             "config": {"rate_per_s": args.serve_rate, "arrival_window_s": args.serve_duration,
                        "horizon_s": args.serve_horizon, "samples_scale": args.serve_samples,
-                       "tick_ops": args.tick_ops, "precision": args.precision, "arena_gb": arena / 1e9,
+                       "tick_ops": args.tick_ops, "chains_per_request": args.serve_chains,
+                       "precision": args.precision, "arena_gb": arena / 1e9,
                        "mix": {k: v for k, v in synth.SERVE_MIX.items()}},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)

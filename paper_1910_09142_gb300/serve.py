@@ -1,9 +1,12 @@
 """Continuous-batching sampling server over the C ABI.
 
-A job asks for ``n_samples`` Markov steps of one hybrid-METTS chain
+A job asks for ``n_samples`` kept samples of the hybrid-METTS chain
 (Sec. I.C.1) with its own parameters (ladder length, cluster size, beta,
-chi_max, ...).  The server keeps every admitted chain's MPS resident on the
-device and, on every tick, advances *all* resident chains by one Markov step
+chi_max, ...), drawn by one or several independent chains (walkers, each
+with its own random stream and warm-up), so that a few large requests still
+fill the GPU's SMs (one CTA per chain).  The server keeps every admitted
+chain's MPS resident on the device and, on every tick, advances *all*
+resident chains by one Markov step
 in one batched call per stage (``hm_evolve``, ``hm_measure_cluster``,
 ``hm_collapse``), whatever their sizes.  Jobs that arrive while others run
 wait in a FIFO queue and are admitted at the next tick boundary as soon as
@@ -34,27 +37,80 @@ from . import binding
 from .estimators import Estimator
 
 
-class Job:
-    """One sampling request; ``results`` gets one observable vector per kept sample."""
+# A job's k-th chain draws from Philox stream chain_id + k * FANOUT_STRIDE, so
+# jobs whose chain ids stay below FANOUT_STRIDE never share a stream.
+FANOUT_STRIDE = 1 << 24
 
-    def __init__(self, job_id, params, n_samples, n_warmup=0, arrival=None, bin_size=10):
-        self.id = job_id
-        self.params = params                 # binding.Params
-        self.n_samples = int(n_samples)
-        self.n_warmup = int(n_warmup)
-        self.arrival = arrival
-        self.admitted = None
-        self.finished = None
+
+class Walker:
+    """One Markov chain of a job: its own random stream, warm-up and share of
+    the job's samples."""
+
+    def __init__(self, job, k, n_keep):
+        self.job = job
+        self.k = k
+        self.params = binding.Params(*[getattr(job.params, f) for f, _ in binding.Params._fields_])
+        self.params.chain_id = (int(job.params.chain_id) + k * FANOUT_STRIDE) & 0xFFFFFFFF
+        self.n_steps = job.n_warmup + int(n_keep)
         self.chain = None
         self.done_steps = 0
         self.results = []                    # observable vectors of kept samples
         self.env = []                        # collapse outcomes of every step
         self.latencies = []                  # seconds per kept sample
+        self.sample_t0 = None                # start of the sample now being evolved
+        self.resume_from = None              # (outcomes, sample index) of a checkpoint
+        self.bytes = 0
+
+    @property
+    def complete(self):
+        return self.done_steps >= self.n_steps
+
+    def checkpoint(self):
+        if self.env:
+            env = [int(x) for x in self.env[-1]]
+        elif self.resume_from is not None:            # resumed, no step since
+            env = [int(x) for x in self.resume_from[0]]
+        else:
+            env = None
+        return dict(env=env, next_sample=self.done_steps, results=[[float(x) for x in r] for r in self.results])
+
+
+class Job:
+    """One sampling request: ``n_samples`` kept samples of the chain of
+    Sec. I.C.1, drawn by ``n_chains`` independent chains (walkers), each
+    with ``n_warmup`` discarded warm-up samples and an equal share of the
+    kept ones (the first n_samples % n_chains walkers keep one more)."""
+
+    def __init__(self, job_id, params, n_samples, n_warmup=0, arrival=None, bin_size=10, n_chains=1):
+        self.id = job_id
+        self.params = params                 # binding.Params
+        self.n_samples = int(n_samples)
+        self.n_warmup = int(n_warmup)
+        self.n_chains = max(1, min(int(n_chains), max(1, self.n_samples)))
+        if int(params.chain_id) >= FANOUT_STRIDE and self.n_chains > 1:
+            raise ValueError("a job with several chains needs chain_id < %d" % FANOUT_STRIDE)
+        self.arrival = arrival
+        self.admitted = None
+        self.finished = None
         self.bytes = 0
         self.bin_size = int(bin_size)
-        self.estimator = None                # Estimator over the kept samples
-        self.resume_from = None              # (outcomes, sample index) of a checkpoint
-        self.sample_t0 = None                # start of the sample now being evolved
+        self.estimator = None                # Estimator over the kept samples of every walker
+        q, r = divmod(self.n_samples, self.n_chains)
+        self.walkers = [Walker(self, k, q + (1 if k < r else 0)) for k in range(self.n_chains)]
+
+    @property
+    def results(self):
+        """Kept observable vectors, walker by walker."""
+        return [x for w in self.walkers for x in w.results]
+
+    @property
+    def env(self):
+        """Collapse outcomes of every step, walker by walker."""
+        return [x for w in self.walkers for x in w.env]
+
+    @property
+    def latencies(self):
+        return [x for w in self.walkers for x in w.latencies]
 
     def estimate(self):
         """Mean of every observable over the kept samples, and its binned
@@ -66,40 +122,37 @@ class Job:
 
     @property
     def complete(self):
-        return self.done_steps >= self.n_warmup + self.n_samples
+        return all(w.complete for w in self.walkers)
 
     def checkpoint(self):
         """Everything needed to continue this job elsewhere, as plain data:
-        its parameters, the outcomes of its last collapse, its sample index
-        and the samples kept so far.  Step 4 resets the cluster to Bell
-        pairs, so no MPS is saved."""
-        if self.env:
-            env = [int(x) for x in self.env[-1]]
-        elif self.resume_from is not None:            # resumed, no step since
-            env = [int(x) for x in self.resume_from[0]]
-        else:
-            env = None
+        its parameters and, per walker, the outcomes of its last collapse,
+        its sample index and the samples kept so far.  Step 4 resets the
+        cluster to Bell pairs, so no MPS is saved."""
         return dict(id=self.id, params={f: getattr(self.params, f) for f, _ in binding.Params._fields_},
-                    env=env, next_sample=self.done_steps, n_samples=self.n_samples, n_warmup=self.n_warmup,
-                    bin_size=self.bin_size, results=[[float(x) for x in r] for r in self.results])
+                    n_samples=self.n_samples, n_warmup=self.n_warmup, n_chains=self.n_chains,
+                    bin_size=self.bin_size, chains=[w.checkpoint() for w in self.walkers])
 
 
 class Server:
     """FIFO admission by arena bytes and batch slots; one batched step per tick."""
 
     def __init__(self, ctx, arena_bytes, max_chains=448, clock=time.perf_counter,
-                 query_memory=None, num_obs=None, num_env=None, sleep=time.sleep, tick_ops=None):
+                 query_memory=None, num_obs=None, num_env=None, sleep=time.sleep, tick_ops=None,
+                 chains_per_job=1):
         self.ctx = ctx
         self.tick_ops = int(tick_ops) if tick_ops else None
         self.capacity = int(arena_bytes)
         self.max_chains = int(max_chains)
+        self.chains_per_job = max(1, int(chains_per_job))
         self.clock = clock
         self.sleep = sleep
         self.query_memory = query_memory or binding.query_memory
         self.num_obs = num_obs or binding.num_obs
         self.num_env = num_env or binding.num_env
         self.queue = collections.deque()
-        self.active = []
+        self.active = []                     # admitted, unfinished jobs
+        self.resident = []                   # their walkers still drawing
         self.finished = []
         self.used = 0
         self.ticks = 0
@@ -108,49 +161,63 @@ class Server:
         self._next_id = 0
 
     # -- requests ---------------------------------------------------------------------
-    def submit(self, params, n_samples, n_warmup=0, arrival=None, job_id=None):
+    def submit(self, params, n_samples, n_warmup=0, arrival=None, job_id=None, n_chains=None):
         """Queue a job; returns it.  ``params`` is a binding.Params; ``arrival``
         (clock time the request came in) defaults to now; ``job_id`` keeps a
-        restored job's identity (default: the next free id)."""
+        restored job's identity (default: the next free id); ``n_chains``
+        walkers share its samples (default: the server's chains_per_job)."""
         jid = self._next_id if job_id is None else int(job_id)
-        job = Job(jid, params, n_samples, n_warmup, self.clock() if arrival is None else arrival)
-        job.bytes = self.query_memory(params)
-        if job.bytes > self.capacity:
-            raise ValueError("job %d needs %d bytes, more than the whole arena" % (job.id, job.bytes))
+        job = Job(jid, params, n_samples, n_warmup, self.clock() if arrival is None else arrival,
+                  n_chains=self.chains_per_job if n_chains is None else n_chains)
+        for w in job.walkers:
+            w.bytes = self.query_memory(w.params)
+        job.bytes = sum(w.bytes for w in job.walkers)
+        if job.bytes > self.capacity or job.n_chains > self.max_chains:
+            raise ValueError("job %d needs %d bytes and %d chains, more than the whole arena"
+                             % (job.id, job.bytes, job.n_chains))
         self._next_id = max(self._next_id, jid + 1)
         self.queue.append(job)
         return job
 
     def resume(self, ckpt):
-        """Queue a job from ``Job.checkpoint()`` data; it continues with the
-        draws the interrupted job would have made (hm_resume_chain)."""
+        """Queue a job from ``Job.checkpoint()`` data; every walker continues
+        with the draws the interrupted one would have made (hm_resume_chain)."""
         job = self.submit(binding.Params(**ckpt["params"]), ckpt["n_samples"], ckpt["n_warmup"],
-                          job_id=ckpt.get("id"))
+                          job_id=ckpt.get("id"), n_chains=ckpt["n_chains"])
         job.bin_size = int(ckpt["bin_size"])
-        job.done_steps = int(ckpt["next_sample"])
-        for r in ckpt["results"]:
-            job.results.append(np.array(r))
-            if job.estimator is None:
-                job.estimator = Estimator(len(r), job.bin_size)
-            job.estimator.add(job.id, r)
-        if job.done_steps > 0:
-            job.resume_from = (np.array(ckpt["env"], dtype=np.int8), job.done_steps)
+        for w, wc in zip(job.walkers, ckpt["chains"]):
+            w.done_steps = int(wc["next_sample"])
+            for r in wc["results"]:
+                w.results.append(np.array(r))
+                if job.estimator is None:
+                    job.estimator = Estimator(len(r), job.bin_size)
+                job.estimator.add((job.id, w.k), r)
+            if w.done_steps > 0:
+                w.resume_from = (np.array(wc["env"], dtype=np.int8), w.done_steps)
         return job
 
     def _admit(self):
-        while self.queue and len(self.active) < self.max_chains:
+        while self.queue:
             job = self.queue[0]
-            if self.used + job.bytes > self.capacity:
+            live = [w for w in job.walkers if not w.complete]
+            need = sum(w.bytes for w in live)
+            if self.used + need > self.capacity or len(self.resident) + len(live) > self.max_chains:
                 break                                  # FIFO: later jobs wait behind it
             self.queue.popleft()
-            if job.resume_from is not None:
-                env, n = job.resume_from
-                job.chain = self.ctx.init_chain(job.params, env_init=env, next_sample=n)
-            else:
-                job.chain = self.ctx.init_chain(job.params)
+            for w in live:
+                if w.resume_from is not None:
+                    env, n = w.resume_from
+                    w.chain = self.ctx.init_chain(w.params, env_init=env, next_sample=n)
+                else:
+                    w.chain = self.ctx.init_chain(w.params)
+                self.used += w.bytes
+                self.resident.append(w)
             job.admitted = self.clock()
-            self.used += job.bytes
-            self.active.append(job)
+            if live:
+                self.active.append(job)
+            else:                                      # nothing left to draw
+                job.finished = job.admitted
+                self.finished.append(job)
 
     def checkpoint(self):
         """Checkpoint of every job, finished, resident or queued, as plain
@@ -178,16 +245,16 @@ class Server:
         Returns the number of chains stepped (0 when idle).
         """
         self._admit()
-        if not self.active:
+        if not self.resident:
             return 0
         t0 = self.clock()
-        ids = [j.chain for j in self.active]
-        for j in self.active:
-            if j.sample_t0 is None:
-                j.sample_t0 = t0
+        ids = [w.chain for w in self.resident]
+        for w in self.resident:
+            if w.sample_t0 is None:
+                w.sample_t0 = t0
         if self.tick_ops:
             done = self.ctx.evolve_partial(ids, self.tick_ops)
-            ready = [j for j, d in zip(self.active, done) if d]
+            ready = [w for w, d in zip(self.resident, done) if d]
             # the slices are asynchronous: wait for them, so that a tick lasts
             # its device time and the next tick's admission sees the clock
             sync = getattr(self.ctx, "synchronize", None)
@@ -195,47 +262,51 @@ class Server:
                 sync()
         else:
             self.ctx.evolve(ids)
-            ready = list(self.active)
+            ready = list(self.resident)
         obs = {}
         for n_obs, group in self._groups(self.num_obs, ready).items():
-            vals = self.ctx.measure([j.chain for j in group], n_obs)
-            for j, v in zip(group, vals):
-                obs[j.id] = v
+            vals = self.ctx.measure([w.chain for w in group], n_obs)
+            for w, v in zip(group, vals):
+                obs[id(w)] = v
         for n_env, group in self._groups(self.num_env, ready).items():
-            env, _ = self.ctx.collapse([j.chain for j in group], n_env)
-            for j, e in zip(group, env):
-                j.env.append(np.array(e))
+            env, _ = self.ctx.collapse([w.chain for w in group], n_env)
+            for w, e in zip(group, env):
+                w.env.append(np.array(e))
         t1 = self.clock()
         self.busy_s += t1 - t0
         self.ticks += 1
         still = []
-        for j in self.active:
-            if j.id not in obs:
-                still.append(j)                        # evolution continues next tick
+        for w in self.resident:
+            if id(w) not in obs:
+                still.append(w)                        # evolution continues next tick
                 continue
-            if j.done_steps >= j.n_warmup:
-                j.results.append(obs[j.id])
-                if j.estimator is None:
-                    j.estimator = Estimator(len(obs[j.id]), j.bin_size)
-                j.estimator.add(j.id, obs[j.id])
-                j.latencies.append(t1 - j.sample_t0)
+            job = w.job
+            if w.done_steps >= job.n_warmup:
+                v = obs[id(w)]
+                w.results.append(v)
+                if job.estimator is None:
+                    job.estimator = Estimator(len(v), job.bin_size)
+                job.estimator.add((job.id, w.k), v)
+                w.latencies.append(t1 - w.sample_t0)
                 self.samples += 1
-            j.sample_t0 = None
-            j.done_steps += 1
-            if j.complete:
-                self.ctx.free_chain(j.chain)
-                self.used -= j.bytes
-                j.finished = t1
-                self.finished.append(j)
+            w.sample_t0 = None
+            w.done_steps += 1
+            if w.complete:
+                self.ctx.free_chain(w.chain)
+                self.used -= w.bytes
             else:
-                still.append(j)
-        self.active = still
+                still.append(w)
+        self.resident = still
+        for job in [j for j in self.active if j.complete]:
+            job.finished = t1
+            self.active.remove(job)
+            self.finished.append(job)
         return len(ids)
 
-    def _groups(self, count, jobs=None):
+    def _groups(self, count, walkers=None):
         groups = collections.OrderedDict()
-        for j in self.active if jobs is None else jobs:
-            groups.setdefault(count(j.params), []).append(j)
+        for w in self.resident if walkers is None else walkers:
+            groups.setdefault(count(w.params), []).append(w)
         return groups
 
     def run(self, arrivals=()):
@@ -246,7 +317,7 @@ class Server:
         tick = 0
         while True:
             while pending and (pending[0][0] <= tick or (not self.active and not self.queue)):
-                _, p, n, w = pending.popleft()
+                _, p, n, w = pending.popleft()[:4]
                 self.submit(p, n, w)
             if self.step() == 0 and not self.queue and not pending:
                 return self.stats()
@@ -280,8 +351,9 @@ class Server:
 
     # -- statistics ---------------------------------------------------------------------
     def stats(self):
-        lat = [x for j in self.finished + self.active for x in j.latencies]
-        waits = [j.admitted - j.arrival for j in self.finished + self.active if j.admitted is not None]
+        jobs = self.finished + self.active
+        lat = [x for j in jobs for x in j.latencies]
+        waits = [j.admitted - j.arrival for j in jobs if j.admitted is not None]
         return {"samples": self.samples, "ticks": self.ticks, "busy_s": self.busy_s,
                 "samples_per_s": self.samples / self.busy_s if self.busy_s > 0 else None,
                 "latency_p50_s": float(np.percentile(lat, 50)) if lat else None,
@@ -289,4 +361,5 @@ class Server:
                 "queue_wait_p50_s": float(np.percentile(waits, 50)) if waits else None,
                 "queue_wait_p99_s": float(np.percentile(waits, 99)) if waits else None,
                 "jobs_finished": len(self.finished), "jobs_resident": len(self.active),
+                "chains_resident": len(self.resident),
                 "jobs_queued": len(self.queue)}

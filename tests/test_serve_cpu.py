@@ -239,7 +239,8 @@ def test_checkpoint_and_resume_continue_the_job_exactly():
     for _ in range(4):
         first.step()
     ckpt = json.loads(json.dumps(job.checkpoint()))        # plain data, survives a round trip
-    assert ckpt["next_sample"] == 4 and len(ckpt["results"]) == 2 and len(ckpt["env"]) == ckpt_env_len(job)
+    c0 = ckpt["chains"][0]
+    assert c0["next_sample"] == 4 and len(c0["results"]) == 2 and len(c0["env"]) == ckpt_env_len(job)
     second = serve.Server(FakeCtx(), 1 << 40)
     again = second.resume(ckpt)
     second.run()
@@ -313,7 +314,7 @@ def test_checkpoint_of_a_resumed_job_before_its_next_step():
     again = other.resume(ckpt)
     assert again.id == job.id and other._next_id == 10
     ckpt2 = again.checkpoint()                          # no step since the resume
-    assert ckpt2["env"] == ckpt["env"] and ckpt2["next_sample"] == 2
+    assert ckpt2["chains"][0]["env"] == ckpt["chains"][0]["env"] and ckpt2["chains"][0]["next_sample"] == 2
     third = serve.Server(FakeCtx(), 1 << 40)
     last = third.resume(ckpt2)
     third.run()
@@ -337,3 +338,46 @@ def test_tick_op_budget_keeps_short_jobs_moving():
     assert short_job.finished is not None and long_job.finished is not None
     assert sliced.ticks == 12                  # 3 samples x 4 ticks of 40 ops for the long chain
     assert len(short_job.results) == 3
+
+
+def test_fanned_out_job_splits_its_samples_over_independent_chains():
+    """A job of 7 samples on 3 walkers: 3 + 2 + 2 kept samples after 1 warm-up
+    each, every walker on its own stream (chain_id + k * 2^24), memory and
+    batch slots for all three, and the same results alone and in a mix."""
+    alone = serve.Server(FakeCtx(), 1 << 40)
+    job = alone.submit(_p(4, 9), 7, 1, n_chains=3)
+    assert [w.n_steps for w in job.walkers] == [4, 3, 3]
+    assert [w.params.chain_id for w in job.walkers] == [9 + k * serve.FANOUT_STRIDE for k in range(3)]
+    assert job.bytes == 3 * binding.query_memory(_p(4, 9))
+    alone.run()
+    assert job.complete and len(job.results) == 7 and job.estimator.count == 7
+    # the fake's observable: 1000 Lx + 10 chain_id + step; warm-up step 0 dropped
+    assert [r[0] for r in job.results] == [1000.0 * 4 + 10.0 * (9 + k * serve.FANOUT_STRIDE) + s
+                                           for k, n in enumerate((3, 2, 2)) for s in range(1, n + 1)]
+    mixed = serve.Server(FakeCtx(), 1 << 40, max_chains=4, chains_per_job=2)
+    other = mixed.submit(_p(3, 1), 5)                       # 2 walkers by the server's default
+    again = mixed.submit(_p(4, 9), 7, 1, n_chains=3)        # waits for slots: 2 + 3 > 4
+    mixed.step()
+    assert len(mixed.resident) == 2 and len(mixed.queue) == 1
+    mixed.run()
+    assert other.n_chains == 2 and len(other.results) == 5
+    assert all(np.array_equal(x, y) for x, y in zip(again.results, job.results)) and len(again.results) == 7
+
+
+def test_fanned_out_job_resumes_every_walker():
+    import json
+    whole = serve.Server(FakeCtx(), 1 << 40)
+    ref = whole.submit(_p(5, 3), 5, 1, n_chains=2)          # walkers of 4 and 3 steps
+    whole.run()
+    first = serve.Server(FakeCtx(), 1 << 40)
+    job = first.submit(_p(5, 3), 5, 1, n_chains=2)
+    for _ in range(3):
+        first.step()
+    ckpt = json.loads(json.dumps(first.checkpoint()))
+    assert [c["next_sample"] for c in ckpt["jobs"][0]["chains"]] == [3, 3]
+    second = serve.Server.restore(ckpt, FakeCtx(), 1 << 40)
+    second.step()                                           # walker 1 is done after this step
+    assert not second.active and not second.resident and second.finished[0].complete
+    again = second.finished[0]
+    assert [list(r) for r in again.results] == [list(r) for r in ref.results]
+    assert np.allclose(again.estimate()[0], np.array(ref.results).mean(axis=0), atol=1e-12)
