@@ -392,6 +392,44 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
+// Tangent t of the Jacobi rotation that makes columns with Gram entries
+// (a, g; g, b) orthogonal: t = sign(z) / (|z| + sqrt(1 + z^2)),
+// z = (b - a) / (2 g) = d / (2 g).  It sits on the critical path of every
+// pass, so it takes the short-latency binary32 forms (approximate divide and
+// reciprocal square root, a few ulp): a rotation is exactly conformal
+// whatever its angle, the stretch c^2 + s^2 - 1 is removed with the column
+// scales when W and V are promoted, and an angle that is off by 1e-7
+// relative leaves an off-diagonal 1e-7 times the one it removed, which the
+// next sweep takes.  The binary64 kernels need it cheaply too:
+// GB300 has few binary64 units, and a binary64 square root or divide is a
+// sequence of them.  The rotation (c, s) = (1, t) / sqrt(1 + t^2) is
+// orthogonal to binary64 rounding whatever t is, so t only has to be close:
+// z is formed in binary32 from d and g scaled by the same power of two (z
+// does not change), which leaves an off-diagonal of relative size ~1e-7
+// times the one it removes, for the next sweep.  Operands too far apart for
+// binary32 take the binary64 formula.
+// Squared column norm below which the binary32 sweeps leave a column alone:
+// a normal number whose square root (1e-15) is far below binary32
+// resolution against columns of order one.  With both norms above it, a
+// rotated pair's |g| > tol sqrt(a b) > 1e-37 is normal too.
+constexpr float kTiny32 = 1e-30f;
+
+__device__ __forceinline__ float jacobi_tangent32(float d, float g) {
+  const float z = __fdividef(d, 2.0f * g);
+  if (fabsf(z) > 1e18f) return __fdividef(0.5f, z);
+  const float w = 1.0f + z * z;
+  return copysignf(__fdividef(1.0f, fabsf(z) + w * rsqrtf(w)), z);
+}
+
+__device__ __forceinline__ double jacobi_tangent64(double d, double g) {
+  int e;
+  frexp(fmax(fabs(d), fabs(g)), &e);
+  const float gf = (float)ldexp(g, -e);
+  if (fabsf(gf) >= 1e-30f) return (double)jacobi_tangent32((float)ldexp(d, -e), gf);
+  const double z = d / (2.0 * g);
+  return fabs(z) > 1e150 ? 0.5 / z : copysign(1.0, z) / (fabs(z) + sqrt(1.0 + z * z));
+}
+
 // Per-group convergence words of a grouped Jacobi (shared memory).
 struct GroupSh {
   int32_t flag[16];
@@ -405,19 +443,26 @@ struct GroupSh {
 // start.  Round-robin pairing: every round's pairs are disjoint.  L lanes
 // work on one pair, so a warp rotates 32 / L pairs at once (more pairs in
 // flight, shorter reductions; the rotations are latency-bound, not
-// arithmetic-bound).  Stops after a sweep with no rotation or whose largest
+// arithmetic-bound).  Binary64 (T = double): the rotation tests compare
+// squares, the stopping rule only asks whether some ratio reached `stop`,
+// and the tangent comes from jacobi_tangent64.  A lane moves its rows in
+// batches of B, every load of a
+// batch issued before the first store (a store to one column could alias the
+// next load of the other, so the compiler keeps them in program order), and
+// its first batch stays in registers from the dot product to the rotation:
+// a pass waits on one memory latency per batch, not one per row.  Stops after a sweep with no rotation or whose largest
 // ratio |g| / sqrt(a b) is below `stop` (the next sweep's off-diagonals are
 // then of order stop^2).  Returns the sweeps, or -1 when max_sweeps ran out.
-template <typename T, typename TV, int L>
+template <typename T, typename TV, int L, int B>
 __device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
   constexpr int PPW = 32 / L;              // pairs per warp at once
+  constexpr bool SC = sizeof(T) == sizeof(double);   // binary64 form of the angle
   const int lane = threadIdx.x & 31;
   const int sub = lane / L, sl = lane % L;
   const int nthr = 32 * nw;
   const T eps = sizeof(T) == sizeof(double) ? T(2.220446049250313e-16) : T(1.1920928955078125e-07);
   const T tol = sqrt((T)q) * eps;
-  const T huge = sizeof(T) == sizeof(double) ? T(1e150) : T(1e18);
   const int p2 = p + (p & 1);
   const int npair = p2 / 2;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
@@ -440,52 +485,122 @@ __device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, TV* __rest
         const int pi = base + sub;
         int a = -1, b = -1;
         if (pi < npair) {
+          const int m = p2 - 1;          // (rd +- pi) mod m, 0 <= rd < m, 0 < pi < m
           if (pi == 0) {
             a = rd;
-            b = p2 - 1;
+            b = m;
           } else {
-            a = (rd + pi) % (p2 - 1);
-            b = (rd - pi + (p2 - 1)) % (p2 - 1);
+            a = rd + pi;
+            if (a >= m) a -= m;
+            b = rd - pi;
+            if (b < 0) b += m;
           }
           if (a >= p || b >= p) a = b = -1;
         }
         T* x = W + (size_t)(a < 0 ? 0 : a) * ldw;
         T* y = W + (size_t)(b < 0 ? 0 : b) * ldw;
-        T g0 = T(0), g1 = T(0);
-        if (a >= 0) {
-          int i = sl;
-          for (; i + L < q; i += 2 * L) {
-            g0 = fma(x[i], y[i], g0);
-            g1 = fma(x[i + L], y[i + L], g1);
-          }
-          if (i < q) g0 = fma(x[i], y[i], g0);
+        // rows sl + u L (u < B) of both columns stay in registers from the
+        // dot product to the rotation; further rows go in batches of B whose
+        // loads are all issued before any use (one memory latency a batch)
+        T x0[B], y0[B], gacc[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          const int i = sl + u * L;
+          const bool in = a >= 0 && i < q;
+          x0[u] = in ? x[i] : T(0);
+          y0[u] = in ? y[i] : T(0);
         }
-        T ga = g0 + g1;
+#pragma unroll
+        for (int u = 0; u < B; ++u) gacc[u] = x0[u] * y0[u];
+        if (a >= 0) {
+          for (int i0 = sl + B * L; i0 < q; i0 += B * L) {
+            T xr[B], yr[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+              const int i = i0 + u * L;
+              xr[u] = i < q ? x[i] : T(0);
+              yr[u] = i < q ? y[i] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) gacc[u] = fma(xr[u], yr[u], gacc[u]);
+          }
+        }
+        T ga = gacc[0];
+#pragma unroll
+        for (int u = 1; u < B; ++u) ga += gacc[u];
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
         bool done = false;
         T na = T(0), nb = T(0);
         if (a >= 0) {
           const T al = nrm[a], be = nrm[b];
-          if (ga != T(0) && al > T(0) && be > T(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-            rmax = fmax(rmax, fabs(ga) / (sqrt(al) * sqrt(be)));
-            const T zeta = (be - al) / (T(2) * ga);
-            T t;
-            if (fabs(zeta) > huge) t = T(0.5) / zeta;
-            else t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-            const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
-            for (int i = sl; i < q; i += L) {
-              const T u = x[i], v = y[i];
-              x[i] = cs * u - sn * v;
-              y[i] = sn * u + cs * v;
+          bool go;
+          T ratio = T(0);
+          if constexpr (SC) {
+            go = ga != T(0) && al > T(0) && be > T(0) && ga * ga > tol * tol * (al * be);
+          } else {
+            // columns below kTiny32 are noise at binary32 resolution, and
+            // the fast reciprocal square root flushes subnormal inputs to 0
+            ratio = fabs(ga) * (rsqrtf(fmax(al, kTiny32)) * rsqrtf(fmax(be, kTiny32)));
+            go = ga != T(0) && al > kTiny32 && be > kTiny32 && ratio > tol;
+          }
+          if (go) {
+            T t, cs;
+            if constexpr (SC) {
+              // binary64 pipe: squared tests, a binary32 tangent, one rsqrt
+              if (ga * ga >= stop * stop * (al * be)) rmax = T(1);
+              t = jacobi_tangent64(be - al, ga);
+              cs = rsqrt(T(1) + t * t);
+            } else {
+              rmax = fmax(rmax, ratio);
+              t = jacobi_tangent32(be - al, ga);
+              cs = rsqrtf(T(1) + t * t);
+            }
+            const T sn = cs * t;
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+              const int i = sl + u * L;
+              if (i < q) {
+                x[i] = cs * x0[u] - sn * y0[u];
+                y[i] = sn * x0[u] + cs * y0[u];
+              }
+            }
+            for (int i0 = sl + B * L; i0 < q; i0 += B * L) {
+              T xr[B], yr[B];
+#pragma unroll
+              for (int u = 0; u < B; ++u) {
+                const int i = i0 + u * L;
+                xr[u] = i < q ? x[i] : T(0);
+                yr[u] = i < q ? y[i] : T(0);
+              }
+#pragma unroll
+              for (int u = 0; u < B; ++u) {
+                const int i = i0 + u * L;
+                if (i < q) {
+                  x[i] = cs * xr[u] - sn * yr[u];
+                  y[i] = sn * xr[u] + cs * yr[u];
+                }
+              }
             }
             TV* vx = V + (size_t)a * ldv;
             TV* vy = V + (size_t)b * ldv;
             const TV cv = (TV)cs, sv = (TV)sn;
-            for (int i = sl; i < p; i += L) {
-              const TV u = vx[i], v = vy[i];
-              vx[i] = cv * u - sv * v;
-              vy[i] = sv * u + cv * v;
+            for (int i0 = sl; i0 < p; i0 += B * L) {
+              TV xr[B], yr[B];
+#pragma unroll
+              for (int u = 0; u < B; ++u) {
+                const int i = i0 + u * L;
+                xr[u] = i < p ? vx[i] : TV(0);
+                yr[u] = i < p ? vy[i] : TV(0);
+              }
+#pragma unroll
+              for (int u = 0; u < B; ++u) {
+                const int i = i0 + u * L;
+                if (i < p) {
+                  vx[i] = cv * xr[u] - sv * yr[u];
+                  vy[i] = sv * xr[u] + cv * yr[u];
+                }
+              }
             }
             na = al - t * ga;
             nb = be + t * ga;
@@ -538,13 +653,17 @@ __device__ __forceinline__ int lanes_per_pair(int q, int p, int nw) {
 // TV: element type of V.  A binary64 polish of a binary32 result may keep V
 // in binary32: V carries binary32 accuracy from the preconditioning sweeps
 // anyway, and the polish's rotations are tiny (angles ~1e-6).
-template <typename T, typename TV = T>
+// B: rows per lane and batch (register budget: 4 B values of T in flight).
+// A lane's rows are rounded up to a multiple of B, and on the binary64 pipe
+// every issued instruction costs the same whatever the lanes' predicates, so
+// the binary64 kernels take B = 2.
+template <typename T, typename TV = T, int B = 4>
 __device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
   const int L = lanes_per_pair(q, p, nw);
-  if (L == 8) return jacobi_lanes<T, TV, 8>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
-  if (L == 16) return jacobi_lanes<T, TV, 16>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
-  return jacobi_lanes<T, TV, 32>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  if (L == 8) return jacobi_lanes<T, TV, 8, B>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  if (L == 16) return jacobi_lanes<T, TV, 16, B>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  return jacobi_lanes<T, TV, 32, B>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
 }
 
 // Warp groups for one wave of charge blocks: every block gets at least one

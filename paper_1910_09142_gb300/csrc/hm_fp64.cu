@@ -417,7 +417,7 @@ __device__ void two_site_op_blocked(ChainDev* c, const OpDev op, int t, Shared& 
     const blk::BlockRec& r = M->b[b];
     blk::gather_block<NT, double, double>(c, op.k, ss, r, c->theta, c->W + r.woff, r.q, c->V + r.voff, r.p);
     __syncthreads();
-    const int sw = blk::jacobi_group<double>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig,
+    const int sw = blk::jacobi_group<double, double, 2>(c->W + r.woff, r.q, r.q, r.p, c->V + r.voff, r.p, c->sig,
                                              threadIdx.x >> 5, NT / 32, 1, 0, gs, 1e-9, kMaxSweeps);
     if (sw < 0) {
       set_error(c, HM_ERR_NUMERIC, t, ctx_err);

@@ -117,7 +117,17 @@ void set_global_error(const char* msg);
 
 // Mixed-precision evolve (hm_mixed.cu); chi_cap = largest bond cap in the
 // batch; polish != 0 finishes every SVD with binary64 sweeps (HM_MIXED).
+// A batch of more chains than SMs with chi_cap <= kPairChiCap goes to
+// launch_evolve_mixed_pair (hm_mixed_pair.cu): two CTAs of 256 threads per
+// SM with kPairBlockSmem of shared memory each.  kPairChiCap: on the S=1
+// ladder at chi = 256 the largest charge block measured needs 106 KB in the
+// binary32 layout (p (q + 1) + p (p + 1) + p values; oracle U(1) chain,
+// Lx = 16, 2W = 8, beta = 1, three samples); a larger block takes the
+// staged global-memory path of the same kernel.
 int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream);
+int launch_evolve_mixed_pair(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream);
+constexpr int kPairChiCap = 256;
+constexpr size_t kPairBlockSmem = 108 * 1024;
 
 // Binary32 GEMM tile of the mixed evolve kernel, and the dynamic shared
 // memory one CTA may opt into on sm_100-class parts (227 KB).
@@ -126,12 +136,13 @@ constexpr size_t kMaxSharedOptIn = 227 * 1024;
 
 // Dynamic shared memory of the mixed evolve kernel at bond cap chi_cap: two
 // column blocks of b columns of the q + p <= 6 chi_cap row panel, plus the
-// cached column norms; b = 16, halved (down to 2) while that exceeds 210 KB.
+// cached column norms; b = 16, halved (down to 2) while that exceeds the
+// budget (210 KB, or kPairBlockSmem with two CTAs per SM).
 // The GEMM tile is the floor.  Writes b to *bcols.
-inline size_t mixed_smem_bytes(int chi_cap, int* bcols) {
+inline size_t mixed_smem_bytes(int chi_cap, int* bcols, size_t budget = 210 * 1024) {
   const size_t qp = 6 * (size_t)chi_cap;
   int b = 16;
-  while (b > 2 && (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float) > 210 * 1024) b /= 2;
+  while (b > 2 && (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float) > budget) b /= 2;
   *bcols = b;
   const size_t bytes = (2 * (size_t)b * qp + 3 * (size_t)chi_cap) * sizeof(float);
   const size_t gemm = 2 * (size_t)kMixedGK * kMixedGM * sizeof(float);

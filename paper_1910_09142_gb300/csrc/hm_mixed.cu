@@ -29,9 +29,17 @@ namespace hm {
 
 namespace {
 
-constexpr int NT = 512;
+// This file builds the kernel twice: one CTA of 512 threads per SM (210 KB
+// of shared memory), and, from hm_mixed_pair.cu, two CTAs of 256 threads per
+// SM (108 KB each) for batches with more chains than SMs.
+#ifndef HM_MIXED_NT
+#define HM_MIXED_NT 512
+#define HM_MIXED_CTAS_PER_SM 1
+#endif
+constexpr int NT = HM_MIXED_NT;
+constexpr int kCtasPerSm = HM_MIXED_CTAS_PER_SM;
 constexpr int kMaxSweeps = 60;
-constexpr int GM = kMixedGM, GN = kMixedGN, GK = kMixedGK;   // binary32 GEMM tile (512 threads, 2x4 outputs each)
+constexpr int GM = kMixedGM, GN = kMixedGN, GK = kMixedGK;   // binary32 GEMM tile (2x4 or 4x4 outputs a thread)
 
 struct Scal {
   double red[NT / 32][2];
@@ -371,8 +379,9 @@ __device__ void promote_v(const float* V32, int ldv, int q, int p, double* W64, 
 }
 
 // Shared memory of the binary32 block Jacobi; the kernel's dynamic shared
-// memory is at least this (and at least the staged fallback's plan).
-constexpr size_t kBlockSmem = 210 * 1024;
+// memory is at least this (and at least the staged fallback's plan).  Two
+// CTAs per SM share the SM's 228 KB.
+constexpr size_t kBlockSmem = kCtasPerSm == 1 ? 210 * 1024 : kPairBlockSmem;
 
 // Stopping rule of the binary64 polish: a sweep whose largest rotation ratio
 // is below this leaves off-diagonals of order its square for the next sweep.
@@ -437,7 +446,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       double* V64 = c->V + r.voff;
       promote_w(W32, r.q, V32, r.p, r.q, r.p, W64, c->sig);
       __syncthreads();
-      const int s64 = polish ? blk::jacobi_group<double, float>(W64, r.q, r.q, r.p, V32, r.p, c->sig, warp, NT / 32,
+      const int s64 = polish ? blk::jacobi_group<double, float, 2>(W64, r.q, r.q, r.p, V32, r.p, c->sig, warp, NT / 32,
                                                                 1, 0, gs, kPolishStop, kMaxSweeps)
                              : 0;
       __syncthreads();
@@ -480,7 +489,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       // in shared memory in binary32; norms of block g in c->sig
       const blk::BlockRec& r = M->b[b0 + g];
       float* V32 = smem + wv.off[g] + (size_t)r.p * (r.q | 1);
-      const int s64 = blk::jacobi_group<double, float>(c->W + r.woff, r.q, r.q, r.p, V32, r.p | 1, c->sig + r.svoff,
+      const int s64 = blk::jacobi_group<double, float, 2>(c->W + r.woff, r.q, r.q, r.p, V32, r.p | 1, c->sig + r.svoff,
                                                        warp - wv.w0[g], wv.nw[g], g + 1, g, gs, kPolishStop,
                                                        kMaxSweeps);
       if (warp == wv.w0[g] && (tid & 31) == 0) wv.sw[g] = wv.sw[g] < 0 ? -1 : (s64 < 0 ? -1 : wv.sw[g] + 1000 * s64);
@@ -523,7 +532,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, int bcols, int polish) {
+__global__ void __launch_bounds__(NT, kCtasPerSm) evolve_mixed_kernel(BatchArg b, OutArg o, int bcols, int polish) {
   extern __shared__ float smem[];
   __shared__ Scal sc;
   __shared__ blk::SplitSh ss;
@@ -544,15 +553,12 @@ __global__ void __launch_bounds__(NT) evolve_mixed_kernel(BatchArg b, OutArg o, 
   }
 }
 
-}  // namespace
-
-int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream) {
-  if (b.n <= 0) return HM_OK;
+// Opt-in to the kernel's dynamic shared memory (per device, cached, under a
+// lock: serving workers may launch from several host threads), then launch.
+int launch_kernel(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream) {
   int bcols = 16;
-  const size_t plan = mixed_smem_bytes(chi_cap, &bcols);
+  const size_t plan = mixed_smem_bytes(chi_cap, &bcols, kBlockSmem);
   const size_t smem = plan > kBlockSmem ? plan : kBlockSmem;
-  // the shared-memory opt-in is per device: cache it per device ordinal,
-  // under a lock (serving workers may launch from several host threads)
   static std::mutex mu;
   static size_t configured[64] = {};
   int dev = 0;
@@ -569,5 +575,38 @@ int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, int pol
   evolve_mixed_kernel<<<b.n, NT, smem, (cudaStream_t)stream>>>(b, o, bcols, polish);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
+
+#if HM_MIXED_CTAS_PER_SM == 1
+// SMs of the current device (cached per device ordinal).
+int sm_count() {
+  static std::mutex mu;
+  static int count[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (count[dev] == 0 && cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    count[dev] = 0;
+  return count[dev];
+}
+#endif
+
+}  // namespace
+
+#if HM_MIXED_CTAS_PER_SM == 1
+// A batch with more chains than SMs whose charge blocks fit half an SM's
+// shared memory runs two chains per SM (hm_mixed_pair.cu): all of them are
+// resident at once, and each SM interleaves two independent CTAs.
+int launch_evolve_mixed(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream) {
+  if (b.n <= 0) return HM_OK;
+  const int sms = sm_count();
+  if (chi_cap <= kPairChiCap && sms > 0 && b.n > sms) return launch_evolve_mixed_pair(b, o, chi_cap, polish, stream);
+  return launch_kernel(b, o, chi_cap, polish, stream);
+}
+#else
+int launch_evolve_mixed_pair(const BatchArg& b, const OutArg& o, int chi_cap, int polish, void* stream) {
+  if (b.n <= 0) return HM_OK;
+  return launch_kernel(b, o, chi_cap, polish, stream);
+}
+#endif
 
 }  // namespace hm

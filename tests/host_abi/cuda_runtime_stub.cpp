@@ -14,6 +14,12 @@ cudaError_t cudaGetDevice(int* d) {
   return cudaSuccess;
 }
 cudaError_t cudaFuncSetAttribute(const void*, enum cudaFuncAttribute, int) { return cudaSuccess; }
+// One SM: in the CPU emulation a batch of two or more binary32 chains takes
+// the two-chains-per-SM kernel, a single chain the one-chain kernel.
+cudaError_t cudaDeviceGetAttribute(int* value, enum cudaDeviceAttr attr, int) {
+  *value = attr == cudaDevAttrMultiProcessorCount ? 1 : 0;
+  return cudaSuccess;
+}
 cudaError_t cudaGetSymbolAddress(void** p, const void* symbol) {
   *p = const_cast<void*>(symbol);
   return cudaSuccess;

@@ -1,7 +1,8 @@
 """Builds libhm_emu.so: the library with its CUDA kernels compiled as host
 C++ (TEST INFRASTRUCTURE; see simt_prelude.h and simt_runtime.cpp).
 
-The kernel sources are copied with two textual rewrites, since host
+The kernel sources are copied with two textual rewrites (applied to an
+included kernel file too), since host
 compilers know neither form: each ``kernel<<<grid, block, smem, stream>>>(args)``
 becomes ``simt::launch(grid, block, smem, [&] { kernel(args); })``, and the
 dynamic shared array ``extern __shared__ T name[];`` becomes a pointer to
@@ -16,10 +17,17 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_1910_09142_gb300", "csrc")
-KERNELS = ("hm_fp64.cu", "hm_mixed.cu")
+KERNELS = ("hm_fp64.cu", "hm_mixed.cu", "hm_mixed_pair.cu")
 
 
 def rewrite(text):
+    # a kernel file that builds another one with different settings
+    # (#define ..., #include "other.cu") gets that file's rewritten text
+    def include(m):
+        with open(os.path.join(CSRC, m.group(1))) as f:
+            return rewrite(f.read())
+    text = re.sub(r'#include "(\w+\.cu)"', include, text)
+
     def launch(m):
         config = ",".join(m.group(2).split(",")[:3])          # grid, block, smem (stream dropped)
         return "simt::launch(%s, [&] { %s(%s); });" % (config, m.group(1), m.group(3))

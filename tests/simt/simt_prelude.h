@@ -148,6 +148,10 @@ inline float max(float a, float b) { return std::fmax(a, b); }
 inline double min(double a, double b) { return std::fmin(a, b); }
 inline double max(double a, double b) { return std::fmax(a, b); }
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+inline float __fdividef(float a, float b) { return a / b; }
+using std::frexp;
+using std::ldexp;
 
 template <class T>
 inline cudaError_t cudaFuncSetAttribute(T* entry, cudaFuncAttribute attr, int value) {

@@ -29,7 +29,7 @@ def ctx():
     import torch
     from paper_1910_09142_gb300 import binding
     assert torch.cuda.is_available()
-    c = binding.Context(16 << 30)
+    c = binding.Context(32 << 30)
     yield c
     c.close()
 
@@ -126,22 +126,47 @@ def test_mixed_and_fp64_chains_in_one_call(ctx):
         ctx.free_chain(c)
 
 
+def test_batch_wider_than_the_gpu_runs_two_chains_per_sm(ctx):
+    """A batch of more binary32 chains than SMs goes to the two-chains-per-SM
+    kernel (256 threads, 108 KB each): 200 small chains (Lx = 3 and 4, mixed
+    cluster sizes) in one call; three of them against the oracle."""
+    import torch
+    b = _b()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = max(200, sms + 8)
+    cfgs = [dict(Lx=3 + i % 2, two_W=2 * (i % 3), J_leg=1.0, J_rung=0.7, beta=0.8, tau=0.1, chi_max=48,
+                 cutoff=1e-10) for i in range(n)]
+    ps = [b.params(**c, precision=b.HM_MIXED, seed=2, chain_id=i) for i, c in enumerate(cfgs)]
+    ids = [ctx.init_chain(p) for p in ps]
+    try:
+        ctx.evolve(ids)
+        for i in (0, n // 2 + 1, n - 1):
+            obs = ctx.measure([ids[i]], b.num_obs(ps[i]))[0]
+            r = ochain.HybridChain(seed=2, chain_id=i, **cfgs[i]).sample()
+            assert abs(obs[0] - r["obs"][0]) < E_RTOL * abs(r["obs"][0])
+            assert np.abs(obs[1:] - r["obs"][1:]).max() < BOND_ATOL
+    finally:
+        for c in ids:
+            ctx.free_chain(c)
+
+
 @pytest.mark.slow
-def test_ladder16_launch_config_sampled_parity(ctx):
-    """Lx=16, 2W=8, chi=256, cutoff 1e-7, beta=1, tau=0.05: 152 chains (odd
-    ones HM_MIXED, even ones HM_MIXED32) in the benchmark's launch shape; two
+@pytest.mark.parametrize("prec", MIXED)
+def test_ladder16_launch_config_sampled_parity(ctx, prec):
+    """Lx=16, 2W=8, chi=256, cutoff 1e-7, beta=1, tau=0.05: 256 chains in the
+    benchmark's launch shape (more chains than SMs: two chains per SM); two
     of them checked against the oracle (about 20 s of CPU each)."""
     import synth
     b = _b()
     cfg = synth.ladder("ladder16")
-    ps = [b.params(**cfg, precision=b.HM_MIXED if i % 2 else b.HM_MIXED32, seed=0, chain_id=i) for i in range(152)]
+    ps = [b.params(**cfg, precision=getattr(b, prec), seed=0, chain_id=i) for i in range(256)]
     ids = [ctx.init_chain(p) for p in ps]
     try:
         ctx.evolve(ids)
         obs = ctx.measure(ids, b.num_obs(ps[0]))
         env, logp = ctx.collapse(ids, b.num_env(ps[0]))
         assert np.all(np.isfinite(obs)) and np.all(np.isfinite(logp))
-        for i in (0, 151):                       # one of each precision
+        for i in (0, 255):
             ref = ochain.HybridChain(seed=0, chain_id=i, **cfg)
             r, margin = _sample_with_margin(ref)
             assert abs(obs[i][0] - r["obs"][0]) < E_RTOL * abs(r["obs"][0])

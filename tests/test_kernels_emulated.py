@@ -292,3 +292,41 @@ def test_partial_evolution_equals_one_evolve(emu):
         assert np.array_equal(e.measure(whole, p), e.measure(sliced, p))
         assert e.collapse(whole, p) == e.collapse(sliced, p)
         e.close()
+
+
+def test_two_chains_per_sm_kernel_matches_the_oracle(emu):
+    """A batch of more binary32 chains than SMs (the emulation reports one SM)
+    runs two chains per SM, 256 threads each (hm_mixed_pair.cu): both chains
+    follow the oracle within the binary32 bars, draw its outcomes, and the
+    kernel is race-free (bit-identical under a shuffled thread order)."""
+    def run(order):
+        old = os.environ.get("SIMT_ORDER")
+        os.environ["SIMT_ORDER"] = order
+        try:
+            e = Emu(emu)
+            ps = [binding.params(**CFG, seed=9, chain_id=k, precision=binding.HM_MIXED) for k in (4, 5)]
+            ids = np.array([e.init(p) for p in ps], dtype=np.int64)
+            P64 = ctypes.POINTER(ctypes.c_int64)
+            e._ok(emu.hm_evolve(e.h, ids.ctypes.data_as(P64), 2))
+            n_obs = binding.num_obs(ps[0])
+            obs = np.zeros((2, n_obs))
+            e._ok(emu.hm_measure_cluster(e.h, ids.ctypes.data_as(P64), 2, obs.ctypes.data_as(ctypes.c_void_p), n_obs))
+            n_env = binding.num_env(ps[0])
+            env, lp = np.zeros((2, max(n_env, 1)), dtype=np.int8), np.zeros(2)
+            e._ok(emu.hm_collapse(e.h, ids.ctypes.data_as(P64), 2, env.ctypes.data_as(ctypes.c_void_p),
+                                  lp.ctypes.data_as(ctypes.c_void_p)))
+            e.close()
+            return obs, env[:, :n_env], lp
+        finally:
+            if old is None:
+                os.environ.pop("SIMT_ORDER", None)
+            else:
+                os.environ["SIMT_ORDER"] = old
+    obs, env, lp = run("forward")
+    for k, cid in enumerate((4, 5)):
+        r = ochain.HybridChain(seed=9, chain_id=cid, **CFG).sample()
+        assert abs(obs[k][0] - r["obs"][0]) < 1e-5 * abs(r["obs"][0])
+        assert np.abs(obs[k][1:] - r["obs"][1:]).max() < 2e-5
+        assert list(env[k]) == r["env_out"]
+    obs2, env2, lp2 = run("random:3")
+    assert np.array_equal(obs, obs2) and np.array_equal(env, env2) and np.array_equal(lp, lp2)
