@@ -405,9 +405,9 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 // sequence of them.  The rotation (c, s) = (1, t) / sqrt(1 + t^2) is
 // orthogonal to binary64 rounding whatever t is, so t only has to be close:
 // z is formed in binary32 from d and g scaled by the same power of two (z
-// does not change), which leaves an off-diagonal of relative size ~1e-7
-// times the one it removes, for the next sweep.  Operands too far apart for
-// binary32 take the binary64 formula.
+// does not change; bits_to_float, integer instructions only), which leaves
+// an off-diagonal of relative size ~1e-7 times the one it removes, for the
+// next sweep.  Operands too far apart for binary32 take the binary64 formula.
 // Squared column norm below which the binary32 sweeps leave a column alone:
 // a normal number whose square root (1e-15) is far below binary32
 // resolution against columns of order one.  With both norms above it, a
@@ -421,11 +421,25 @@ __device__ __forceinline__ float jacobi_tangent32(float d, float g) {
   return copysignf(__fdividef(1.0f, fabsf(z) + w * rsqrtf(w)), z);
 }
 
+// Biased binary64 exponent of x (0 for zero and subnormals).
+__device__ __forceinline__ int bexp64(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+// x * 2^(1023 - e) as a binary32 number, built from the bits of x by integer
+// instructions (no binary64 or conversion instruction): the top 23 bits of
+// the mantissa, truncated (relative error < 2^-23).  0 when x is zero,
+// subnormal, or 2^126 or more below 2^(e - 1023).  e >= the exponent of x.
+__device__ __forceinline__ float bits_to_float(double x, int e) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  const int ef = ex - e + 127;
+  if (ex == 0 || ef <= 0) return 0.0f;
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
 __device__ __forceinline__ double jacobi_tangent64(double d, double g) {
-  int e;
-  frexp(fmax(fabs(d), fabs(g)), &e);
-  const float gf = (float)ldexp(g, -e);
-  if (fabsf(gf) >= 1e-30f) return (double)jacobi_tangent32((float)ldexp(d, -e), gf);
+  const int e = max(bexp64(d), bexp64(g));
+  const float gf = bits_to_float(g, e);
+  if (fabsf(gf) >= 1e-30f) return (double)jacobi_tangent32(bits_to_float(d, e), gf);
   const double z = d / (2.0 * g);
   return fabs(z) > 1e150 ? 0.5 / z : copysign(1.0, z) / (fabs(z) + sqrt(1.0 + z * z));
 }
@@ -443,9 +457,11 @@ struct GroupSh {
 // start.  Round-robin pairing: every round's pairs are disjoint.  L lanes
 // work on one pair, so a warp rotates 32 / L pairs at once (more pairs in
 // flight, shorter reductions; the rotations are latency-bound, not
-// arithmetic-bound).  Binary64 (T = double): the rotation tests compare
-// squares, the stopping rule only asks whether some ratio reached `stop`,
-// and the tangent comes from jacobi_tangent64.  A lane moves its rows in
+// arithmetic-bound).  Binary64 (T = double): the rotation tests and the
+// tangent take binary32 values built from the operands' bits, so that a
+// pass spends its binary64 instructions on the rotation itself (GB300 runs
+// binary64 at about 1/64 of the binary32 rate); the stopping rule only asks
+// whether some ratio reached `stop`.  A lane moves its rows in
 // batches of B, every load of a
 // batch issued before the first store (a store to one column could alias the
 // next load of the other, so the compiler keeps them in program order), and
@@ -536,8 +552,17 @@ __device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, TV* __rest
           const T al = nrm[a], be = nrm[b];
           bool go;
           T ratio = T(0);
+          float rf = 0.0f;
           if constexpr (SC) {
-            go = ga != T(0) && al > T(0) && be > T(0) && ga * ga > tol * tol * (al * be);
+            // |g| / sqrt(a b) in binary32 from the operands' bits (integer
+            // pipe), each scaled by its own power of two: a, b in [1, 2), g
+            // by the mean exponent, so the ratio holds over the whole
+            // binary64 range and no pair is skipped for its columns' sizes
+            const int ea = bexp64(al), eb = bexp64(be);
+            const float af = bits_to_float(al, ea), bf = bits_to_float(be, eb);
+            rf = fabsf(bits_to_float(ga, (ea + eb) >> 1)) * rsqrtf(fmax(af * bf, 1.0f));
+            if ((ea + eb) & 1) rf *= 0.70710678f;
+            go = ga != T(0) && af > 0.0f && bf > 0.0f && rf > (float)tol;
           } else {
             // columns below kTiny32 are noise at binary32 resolution, and
             // the fast reciprocal square root flushes subnormal inputs to 0
@@ -547,8 +572,8 @@ __device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, TV* __rest
           if (go) {
             T t, cs;
             if constexpr (SC) {
-              // binary64 pipe: squared tests, a binary32 tangent, one rsqrt
-              if (ga * ga >= stop * stop * (al * be)) rmax = T(1);
+              // binary64 pipe: b - a, 1 + t^2, one rsqrt, s = c t
+              if (rf >= (float)stop) rmax = T(1);
               t = jacobi_tangent64(be - al, ga);
               cs = rsqrt(T(1) + t * t);
             } else {

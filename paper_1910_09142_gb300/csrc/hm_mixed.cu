@@ -361,18 +361,23 @@ __device__ void column_scales(const float* V32, int ldv, int p, double* scale) {
 }
 
 // After the binary32 sweeps: W64 = W32 with unit-column scales, V32 scaled
-// in place to unit columns.  scale: p doubles.
+// in place to unit columns (a binary32 product: V32 holds binary32 values
+// anyway, and the binary64 pipe is GB300's scarce one).  scale: p doubles.
 __device__ void promote_w(const float* W32, int ldw, float* V32, int ldv, int q, int p, double* W64, double* scale) {
   column_scales(V32, ldv, p, scale);
   for (int e = threadIdx.x; e < q * p; e += NT) W64[e] = (double)W32[(size_t)(e / q) * ldw + e % q] * scale[e / q];
-  for (int e = threadIdx.x; e < p * p; e += NT) {
-    float* v = V32 + (size_t)(e / p) * ldv + e % p;
-    *v = (float)((double)*v * scale[e / p]);
-  }
+  for (int e = threadIdx.x; e < p * p; e += NT) V32[(size_t)(e / p) * ldv + e % p] *= (float)scale[e / p];
 }
 
-// After the polish (if any): V64 = V32 with unit columns, W64 scaled alike.
-__device__ void promote_v(const float* V32, int ldv, int q, int p, double* W64, double* V64, double* scale) {
+// After the polish: V64 = V32 with unit columns, W64 scaled alike (the
+// binary64 sweep's rotations are binary32 in V).  Without a polish V32 has
+// unit columns from promote_w already and is only widened.
+__device__ void promote_v(const float* V32, int ldv, int q, int p, double* W64, double* V64, double* scale,
+                          int rescale) {
+  if (!rescale) {
+    for (int e = threadIdx.x; e < p * p; e += NT) V64[e] = (double)V32[(size_t)(e / p) * ldv + e % p];
+    return;
+  }
   column_scales(V32, ldv, p, scale);
   for (int e = threadIdx.x; e < q * p; e += NT) W64[e] *= scale[e / q];
   for (int e = threadIdx.x; e < p * p; e += NT) V64[e] = (double)V32[(size_t)(e / p) * ldv + e % p] * scale[e / p];
@@ -450,7 +455,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
                                                                 1, 0, gs, kPolishStop, kMaxSweeps)
                              : 0;
       __syncthreads();
-      promote_v(V32, r.p, r.q, r.p, W64, V64, c->sig);
+      promote_v(V32, r.p, r.q, r.p, W64, V64, c->sig, polish);
       if (s64 < 0) {
         set_error(c, HM_ERR_NUMERIC, t, ctx_err);
         return;
@@ -498,7 +503,7 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
     for (int i = 0; i < n; ++i) {
       const blk::BlockRec& r = M->b[b0 + i];
       const float* V32 = smem + wv.off[i] + (size_t)r.p * (r.q | 1);
-      promote_v(V32, r.p | 1, r.q, r.p, c->W + r.woff, c->V + r.voff, c->sig + r.svoff);
+      promote_v(V32, r.p | 1, r.q, r.p, c->W + r.woff, c->V + r.voff, c->sig + r.svoff, polish);
       __syncthreads();
     }
     for (int i = 0; i < n; ++i) {

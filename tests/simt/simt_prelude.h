@@ -150,6 +150,16 @@ inline double max(double a, double b) { return std::fmax(a, b); }
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 inline float __fdividef(float a, float b) { return a / b; }
+inline int __double2hiint(double x) {
+  unsigned long long b;
+  std::memcpy(&b, &x, 8);
+  return (int)(unsigned)(b >> 32);
+}
+inline int __double2loint(double x) {
+  unsigned long long b;
+  std::memcpy(&b, &x, 8);
+  return (int)(unsigned)(b & 0xffffffffull);
+}
 using std::frexp;
 using std::ldexp;
 
