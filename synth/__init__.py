@@ -48,6 +48,24 @@ def env_draws(n_env, seed):
     return np.random.default_rng(seed).integers(0, 3, size=n_env).astype(np.int8)
 
 
+# Uneven batch: chains of mixed ladder length, cluster size, temperature and
+# bond cap in one batch.
+UNEVEN_MIX = dict(Lx=(8, 16, 24, 32), two_W=(4, 8), beta=(0.5, 16.0), chi_max=(64, 128, 256, 512),
+                  tau=0.05, cutoff=1e-7, J_leg=1.0, J_rung=1.0)
+
+
+def uneven_batch(n, seed, mix=None):
+    """Seeded list of n ladder parameter dicts: Lx, two_W and chi_max
+    uniform over the mix's choices, beta log-uniform over its range."""
+    mix = dict(UNEVEN_MIX if mix is None else mix)
+    rng = np.random.default_rng(seed)
+    lo, hi = mix["beta"]
+    return [dict(Lx=int(rng.choice(mix["Lx"])), two_W=int(rng.choice(mix["two_W"])),
+                 beta=float(np.exp(rng.uniform(np.log(lo), np.log(hi)))), tau=mix["tau"],
+                 chi_max=int(rng.choice(mix["chi_max"])), cutoff=mix["cutoff"],
+                 J_leg=mix["J_leg"], J_rung=mix["J_rung"]) for _ in range(n)]
+
+
 # Serving workload: a Poisson stream of sampling requests of mixed sizes.
 SERVE_MIX = dict(Lx=(8, 16, 32), two_W=(4, 8), beta=(0.5, 16.0), chi_max=(128, 256, 512),
                  samples=(100, 2000), tau=0.05, cutoff=1e-7, J_leg=1.0, J_rung=1.0)

@@ -196,3 +196,22 @@ def test_susceptibility_workspace_is_optional(lib):
     p.no_susceptibility = 2
     with pytest.raises(binding.HmError):
         binding.num_obs(p)
+
+
+def test_large_and_uneven_workloads_fit_their_memory_budgets(lib):
+    """The Lx = 32, chi = 512 ladder (128 chains) and the uneven batch of 1024
+    chains (Lx in {8, 16, 24, 32}, 2W in {4, 8}, beta log-uniform on
+    [0.5, 16], chi_max in {64, 128, 256, 512}) are accepted by the planner and
+    fit the 180 GB the workloads allow, by the library's own memory query; the
+    uneven batch's op lists span two orders of magnitude, which is why launches
+    go costliest chain first and serving slices evolutions per tick."""
+    import synth
+    p32 = binding.params(**synth.ladder("ladder32"), precision=binding.HM_MIXED)
+    assert 128 * binding.query_memory(p32) < 180e9
+    assert len(binding.plan(p32)) > 0
+    batch = [binding.params(**cfg, precision=binding.HM_MIXED, chain_id=i)
+             for i, cfg in enumerate(synth.uneven_batch(1024, seed=0))]
+    total = sum(binding.query_memory(p) for p in batch)
+    ops = [len(binding.plan(p)) for p in batch]
+    assert total < 180e9
+    assert min(ops) > 0 and max(ops) > 50 * min(ops)
