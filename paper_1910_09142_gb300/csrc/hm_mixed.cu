@@ -394,6 +394,13 @@ constexpr size_t kBlockSmem = kCtasPerSm == 1 ? 210 * 1024 : kPairBlockSmem;
 // the polish with off-diagonals of order 1e-12.
 constexpr double kPolishStop = 1e-5;
 
+// Stopping ratio of the binary32 sweeps (warp-group path): 2e-4 when they
+// are the whole SVD (HM_MIXED32; the next sweep's off-diagonals would be
+// ~4e-8, below binary32 resolution), 1e-3 when a binary64 sweep follows
+// (HM_MIXED): the off-diagonals it inherits are then ~1e-6, below
+// kPolishStop, so one binary64 sweep still ends the polish.
+constexpr float kStop32 = 2e-4f, kStop32Polished = 1e-3f;
+
 // One two-site op (step 2 of Sec. I.C.1) in charge blocks (Sec. II.C):
 // theta and the gate in binary32 (operands rounded from the binary64 site
 // tensors, binary32 accumulation, gate coefficients as binary32 pairs); the
@@ -478,7 +485,8 @@ __device__ void two_site_op_mixed(ChainDev* c, const OpDev op, int t, int bcols,
       float* W32 = smem + wv.off[g];
       float* V32 = W32 + (size_t)r.p * (r.q | 1);
       const int sw = blk::jacobi_group<float>(W32, r.q, r.q | 1, r.p, V32, r.p | 1, V32 + (size_t)r.p * (r.p | 1),
-                                              warp - wv.w0[g], wv.nw[g], g + 1, g, gs, 2e-4f, kMaxSweeps);
+                                              warp - wv.w0[g], wv.nw[g], g + 1, g, gs,
+                                              polish ? kStop32Polished : kStop32, kMaxSweeps);
       if (warp == wv.w0[g] && (tid & 31) == 0) wv.sw[g] = sw;
     }
     __syncthreads();
