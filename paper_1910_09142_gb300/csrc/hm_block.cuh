@@ -450,6 +450,152 @@ struct GroupSh {
   uint32_t rbits[16];                     // largest rotation ratio of the sweep, binary32 bits
 };
 
+// One pass: the L lanes of this lane's pair (a, b) (a < 0: no pair) take the
+// dot product of the two columns, the rotation angle and the rotation of W
+// and V, then the pair's first lane stores the two new norms.  Every lane of
+// the warp takes part (the reductions are warp shuffles).  A lane moves its
+// rows in batches of B, every load of a batch issued before the first store
+// (a store to one column could alias the next load of the other, so the
+// compiler keeps them in program order), and its first batch stays in
+// registers from the dot product to the rotation: a pass waits on one memory
+// latency per batch, not one per row.  Binary64 (T = double): the rotation
+// tests and the tangent take binary32 values built from the operands' bits,
+// so that a pass spends its binary64 instructions on the rotation itself
+// (GB300 runs binary64 at about 1/64 of the binary32 rate).  rmax: largest
+// ratio |g| / sqrt(a b) seen (binary64: 1 once some ratio reached `stop`);
+// rot: set when a rotation was applied.
+template <typename T, typename TV, int L, int B>
+__device__ __forceinline__ void jacobi_pass(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
+                                            T* __restrict__ nrm, int a, int b, int sl, T tol, T stop, T& rmax,
+                                            int& rot) {
+  constexpr bool SC = sizeof(T) == sizeof(double);   // binary64 form of the angle
+          T* x = W + (size_t)(a < 0 ? 0 : a) * ldw;
+          T* y = W + (size_t)(b < 0 ? 0 : b) * ldw;
+          // rows sl + u L (u < B) of both columns stay in registers from the
+          // dot product to the rotation; further rows go in batches of B whose
+          // loads are all issued before any use (one memory latency a batch)
+          T x0[B], y0[B], gacc[B];
+  #pragma unroll
+          for (int u = 0; u < B; ++u) {
+            const int i = sl + u * L;
+            const bool in = a >= 0 && i < q;
+            x0[u] = in ? x[i] : T(0);
+            y0[u] = in ? y[i] : T(0);
+          }
+  #pragma unroll
+          for (int u = 0; u < B; ++u) gacc[u] = x0[u] * y0[u];
+          if (a >= 0) {
+            for (int i0 = sl + B * L; i0 < q; i0 += B * L) {
+              T xr[B], yr[B];
+  #pragma unroll
+              for (int u = 0; u < B; ++u) {
+                const int i = i0 + u * L;
+                xr[u] = i < q ? x[i] : T(0);
+                yr[u] = i < q ? y[i] : T(0);
+              }
+  #pragma unroll
+              for (int u = 0; u < B; ++u) gacc[u] = fma(xr[u], yr[u], gacc[u]);
+            }
+          }
+          T ga = gacc[0];
+  #pragma unroll
+          for (int u = 1; u < B; ++u) ga += gacc[u];
+  #pragma unroll
+          for (int o = L / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          bool done = false;
+          T na = T(0), nb = T(0);
+          if (a >= 0) {
+            const T al = nrm[a], be = nrm[b];
+            bool go;
+            T ratio = T(0);
+            float rf = 0.0f;
+            if constexpr (SC) {
+              // |g| / sqrt(a b) in binary32 from the operands' bits (integer
+              // pipe), each scaled by its own power of two: a, b in [1, 2), g
+              // by the mean exponent, so the ratio holds over the whole
+              // binary64 range and no pair is skipped for its columns' sizes
+              const int ea = bexp64(al), eb = bexp64(be);
+              const float af = bits_to_float(al, ea), bf = bits_to_float(be, eb);
+              rf = fabsf(bits_to_float(ga, (ea + eb) >> 1)) * rsqrtf(fmax(af * bf, 1.0f));
+              if ((ea + eb) & 1) rf *= 0.70710678f;
+              go = ga != T(0) && af > 0.0f && bf > 0.0f && rf > (float)tol;
+            } else {
+              // columns below kTiny32 are noise at binary32 resolution, and
+              // the fast reciprocal square root flushes subnormal inputs to 0
+              ratio = fabs(ga) * (rsqrtf(fmax(al, kTiny32)) * rsqrtf(fmax(be, kTiny32)));
+              go = ga != T(0) && al > kTiny32 && be > kTiny32 && ratio > tol;
+            }
+            if (go) {
+              T t, cs;
+              if constexpr (SC) {
+                // binary64 pipe: b - a, 1 + t^2, one rsqrt, s = c t
+                if (rf >= (float)stop) rmax = T(1);
+                t = jacobi_tangent64(be - al, ga);
+                cs = rsqrt(T(1) + t * t);
+              } else {
+                rmax = fmax(rmax, ratio);
+                t = jacobi_tangent32(be - al, ga);
+                cs = rsqrtf(T(1) + t * t);
+              }
+              const T sn = cs * t;
+  #pragma unroll
+              for (int u = 0; u < B; ++u) {
+                const int i = sl + u * L;
+                if (i < q) {
+                  x[i] = cs * x0[u] - sn * y0[u];
+                  y[i] = sn * x0[u] + cs * y0[u];
+                }
+              }
+              for (int i0 = sl + B * L; i0 < q; i0 += B * L) {
+                T xr[B], yr[B];
+  #pragma unroll
+                for (int u = 0; u < B; ++u) {
+                  const int i = i0 + u * L;
+                  xr[u] = i < q ? x[i] : T(0);
+                  yr[u] = i < q ? y[i] : T(0);
+                }
+  #pragma unroll
+                for (int u = 0; u < B; ++u) {
+                  const int i = i0 + u * L;
+                  if (i < q) {
+                    x[i] = cs * xr[u] - sn * yr[u];
+                    y[i] = sn * xr[u] + cs * yr[u];
+                  }
+                }
+              }
+              TV* vx = V + (size_t)a * ldv;
+              TV* vy = V + (size_t)b * ldv;
+              const TV cv = (TV)cs, sv = (TV)sn;
+              for (int i0 = sl; i0 < p; i0 += B * L) {
+                TV xr[B], yr[B];
+  #pragma unroll
+                for (int u = 0; u < B; ++u) {
+                  const int i = i0 + u * L;
+                  xr[u] = i < p ? vx[i] : TV(0);
+                  yr[u] = i < p ? vy[i] : TV(0);
+                }
+  #pragma unroll
+                for (int u = 0; u < B; ++u) {
+                  const int i = i0 + u * L;
+                  if (i < p) {
+                    vx[i] = cv * xr[u] - sv * yr[u];
+                    vy[i] = sv * xr[u] + cv * yr[u];
+                  }
+                }
+              }
+              na = al - t * ga;
+              nb = be + t * ga;
+              done = true;
+              rot = 1;
+            }
+          }
+          __syncwarp();              // every lane of the pair has read the old norms
+          if (done && sl == 0) {
+            nrm[a] = na;
+            nrm[b] = nb;
+          }
+}
+
 // One-sided (Hestenes) Jacobi run by a group of nw warps (warp lw of the
 // group, barrier id bar): W (q x p column-major, q >= p, leading dimension
 // ldw), rotations accumulated into V (p x p, leading dimension ldv, holds the
@@ -457,23 +603,14 @@ struct GroupSh {
 // start.  Round-robin pairing: every round's pairs are disjoint.  L lanes
 // work on one pair, so a warp rotates 32 / L pairs at once (more pairs in
 // flight, shorter reductions; the rotations are latency-bound, not
-// arithmetic-bound).  Binary64 (T = double): the rotation tests and the
-// tangent take binary32 values built from the operands' bits, so that a
-// pass spends its binary64 instructions on the rotation itself (GB300 runs
-// binary64 at about 1/64 of the binary32 rate); the stopping rule only asks
-// whether some ratio reached `stop`.  A lane moves its rows in
-// batches of B, every load of a
-// batch issued before the first store (a store to one column could alias the
-// next load of the other, so the compiler keeps them in program order), and
-// its first batch stays in registers from the dot product to the rotation:
-// a pass waits on one memory latency per batch, not one per row.  Stops after a sweep with no rotation or whose largest
-// ratio |g| / sqrt(a b) is below `stop` (the next sweep's off-diagonals are
-// then of order stop^2).  Returns the sweeps, or -1 when max_sweeps ran out.
+// arithmetic-bound); each pair's work is one jacobi_pass.  Stops after a
+// sweep with no rotation or whose largest ratio |g| / sqrt(a b) is below
+// `stop` (the next sweep's off-diagonals are then of order stop^2).  Returns
+// the sweeps, or -1 when max_sweeps ran out.
 template <typename T, typename TV, int L, int B>
 __device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
   constexpr int PPW = 32 / L;              // pairs per warp at once
-  constexpr bool SC = sizeof(T) == sizeof(double);   // binary64 form of the angle
   const int lane = threadIdx.x & 31;
   const int sub = lane / L, sl = lane % L;
   const int nthr = 32 * nw;
@@ -513,135 +650,103 @@ __device__ int jacobi_lanes(T* __restrict__ W, int q, int ldw, int p, TV* __rest
           }
           if (a >= p || b >= p) a = b = -1;
         }
-        T* x = W + (size_t)(a < 0 ? 0 : a) * ldw;
-        T* y = W + (size_t)(b < 0 ? 0 : b) * ldw;
-        // rows sl + u L (u < B) of both columns stay in registers from the
-        // dot product to the rotation; further rows go in batches of B whose
-        // loads are all issued before any use (one memory latency a batch)
-        T x0[B], y0[B], gacc[B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) {
-          const int i = sl + u * L;
-          const bool in = a >= 0 && i < q;
-          x0[u] = in ? x[i] : T(0);
-          y0[u] = in ? y[i] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < B; ++u) gacc[u] = x0[u] * y0[u];
-        if (a >= 0) {
-          for (int i0 = sl + B * L; i0 < q; i0 += B * L) {
-            T xr[B], yr[B];
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-              const int i = i0 + u * L;
-              xr[u] = i < q ? x[i] : T(0);
-              yr[u] = i < q ? y[i] : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < B; ++u) gacc[u] = fma(xr[u], yr[u], gacc[u]);
-          }
-        }
-        T ga = gacc[0];
-#pragma unroll
-        for (int u = 1; u < B; ++u) ga += gacc[u];
-#pragma unroll
-        for (int o = L / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        bool done = false;
-        T na = T(0), nb = T(0);
-        if (a >= 0) {
-          const T al = nrm[a], be = nrm[b];
-          bool go;
-          T ratio = T(0);
-          float rf = 0.0f;
-          if constexpr (SC) {
-            // |g| / sqrt(a b) in binary32 from the operands' bits (integer
-            // pipe), each scaled by its own power of two: a, b in [1, 2), g
-            // by the mean exponent, so the ratio holds over the whole
-            // binary64 range and no pair is skipped for its columns' sizes
-            const int ea = bexp64(al), eb = bexp64(be);
-            const float af = bits_to_float(al, ea), bf = bits_to_float(be, eb);
-            rf = fabsf(bits_to_float(ga, (ea + eb) >> 1)) * rsqrtf(fmax(af * bf, 1.0f));
-            if ((ea + eb) & 1) rf *= 0.70710678f;
-            go = ga != T(0) && af > 0.0f && bf > 0.0f && rf > (float)tol;
-          } else {
-            // columns below kTiny32 are noise at binary32 resolution, and
-            // the fast reciprocal square root flushes subnormal inputs to 0
-            ratio = fabs(ga) * (rsqrtf(fmax(al, kTiny32)) * rsqrtf(fmax(be, kTiny32)));
-            go = ga != T(0) && al > kTiny32 && be > kTiny32 && ratio > tol;
-          }
-          if (go) {
-            T t, cs;
-            if constexpr (SC) {
-              // binary64 pipe: b - a, 1 + t^2, one rsqrt, s = c t
-              if (rf >= (float)stop) rmax = T(1);
-              t = jacobi_tangent64(be - al, ga);
-              cs = rsqrt(T(1) + t * t);
-            } else {
-              rmax = fmax(rmax, ratio);
-              t = jacobi_tangent32(be - al, ga);
-              cs = rsqrtf(T(1) + t * t);
-            }
-            const T sn = cs * t;
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-              const int i = sl + u * L;
-              if (i < q) {
-                x[i] = cs * x0[u] - sn * y0[u];
-                y[i] = sn * x0[u] + cs * y0[u];
-              }
-            }
-            for (int i0 = sl + B * L; i0 < q; i0 += B * L) {
-              T xr[B], yr[B];
-#pragma unroll
-              for (int u = 0; u < B; ++u) {
-                const int i = i0 + u * L;
-                xr[u] = i < q ? x[i] : T(0);
-                yr[u] = i < q ? y[i] : T(0);
-              }
-#pragma unroll
-              for (int u = 0; u < B; ++u) {
-                const int i = i0 + u * L;
-                if (i < q) {
-                  x[i] = cs * xr[u] - sn * yr[u];
-                  y[i] = sn * xr[u] + cs * yr[u];
-                }
-              }
-            }
-            TV* vx = V + (size_t)a * ldv;
-            TV* vy = V + (size_t)b * ldv;
-            const TV cv = (TV)cs, sv = (TV)sn;
-            for (int i0 = sl; i0 < p; i0 += B * L) {
-              TV xr[B], yr[B];
-#pragma unroll
-              for (int u = 0; u < B; ++u) {
-                const int i = i0 + u * L;
-                xr[u] = i < p ? vx[i] : TV(0);
-                yr[u] = i < p ? vy[i] : TV(0);
-              }
-#pragma unroll
-              for (int u = 0; u < B; ++u) {
-                const int i = i0 + u * L;
-                if (i < p) {
-                  vx[i] = cv * xr[u] - sv * yr[u];
-                  vy[i] = sv * xr[u] + cv * yr[u];
-                }
-              }
-            }
-            na = al - t * ga;
-            nb = be + t * ga;
-            done = true;
-            rot = 1;
-          }
-        }
-        __syncwarp();              // every lane of the pair has read the old norms
-        if (done && sl == 0) {
-          nrm[a] = na;
-          nrm[b] = nb;
-        }
+        jacobi_pass<T, TV, L, B>(W, q, ldw, p, V, ldv, nrm, a, b, sl, tol, stop, rmax, rot);
       }
       group_sync(bar, nthr);
     }
     // warp max of the ratios, then one atomic per warp
+    float rm32 = (float)rmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rm32 = fmaxf(rm32, __shfl_xor_sync(0xffffffffu, rm32, o));
+    const int anyrot = __any_sync(0xffffffffu, rot);
+    if (lane == 0) {
+      if (anyrot) atomicMax(&gs.flag[g], 1);
+      atomicMax(&gs.rbits[g], __float_as_uint(rm32));
+    }
+    group_sync(bar, nthr);
+    const int any = gs.flag[g];
+    const T rm = (T)__uint_as_float(gs.rbits[g]);
+    group_sync(bar, nthr);
+    if (!any || rm < stop) return sweep;
+  }
+  return -1;
+}
+
+// Block-ordered one-sided Jacobi for the binary32 sweeps.  The columns form
+// super-columns of C = 4, and the round-robin tournament pairs the
+// super-columns (ns2 - 1 super-rounds, ns2 = super-columns rounded up to
+// even).  A warp owns the eight columns of its super-pair for a whole
+// super-round.  It rotates every column of one super-column against every
+// column of the other: four sub-rounds of four disjoint pairs, one pair per
+// 8 lanes.  In the first super-round it also rotates the pairs inside both
+// super-columns (three sub-rounds).  Only __syncwarp separates its
+// sub-rounds.  A sweep still visits every pair once, as in jacobi_lanes,
+// with the same passes per warp, but waits at ns2 - 1 group barriers
+// instead of p - 1: the barrier, not the arithmetic, was what the sweeps
+// waited on.  Same arguments, stopping rule and result as jacobi_lanes.
+template <typename T, typename TV, int B>
+__device__ int jacobi_blocks(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
+                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
+  constexpr int L = 8, C = 4;              // 32 / L = C pairs per pass
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / L, sl = lane % L;
+  const int nthr = 32 * nw;
+  const T eps = sizeof(T) == sizeof(double) ? T(2.220446049250313e-16) : T(1.1920928955078125e-07);
+  const T tol = sqrt((T)q) * eps;
+  const int ns = (p + C - 1) / C, ns2 = ns + (ns & 1), nsp = ns2 / 2;
+  for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
+    for (int j = lw; j < p; j += nw) {
+      const T* cj = W + (size_t)j * ldw;
+      T s2 = T(0);
+      for (int i = lane; i < q; i += 32) s2 = fma(cj[i], cj[i], s2);
+      s2 = warp_sum_t(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
+    if (lw == 0 && lane == 0) {
+      gs.flag[g] = 0;
+      gs.rbits[g] = 0u;
+    }
+    group_sync(bar, nthr);
+    T rmax = T(0);
+    int rot = 0;
+    for (int sr = 0; sr < ns2 - 1; ++sr) {
+      for (int sp = lw; sp < nsp; sp += nw) {                       // warp-uniform
+        const int m = ns2 - 1;             // (sr +- sp) mod m, as for the columns
+        int A, Bc;
+        if (sp == 0) {
+          A = sr;
+          Bc = m;
+        } else {
+          A = sr + sp;
+          if (A >= m) A -= m;
+          Bc = sr - sp;
+          if (Bc < 0) Bc += m;
+        }
+        const bool okA = A < ns, okB = Bc < ns;                     // ns2 > ns: one padding super-column
+        if (sr == 0) {
+          // pairs inside A (lanes 0-15) and inside B (lanes 16-31): the
+          // round robin of four columns, (k, 3) and ((k + 1) % 3, (k + 2) % 3)
+          const int base = (sub < 2 ? A : Bc) * C;
+          const bool ok = sub < 2 ? okA : okB;
+          for (int k = 0; k < C - 1; ++k) {
+            int a = base + ((sub & 1) == 0 ? k : (k + 1) % (C - 1));
+            int b = base + ((sub & 1) == 0 ? C - 1 : (k + 2) % (C - 1));
+            if (!ok || a >= p || b >= p) a = b = -1;
+            jacobi_pass<T, TV, L, B>(W, q, ldw, p, V, ldv, nrm, a, b, sl, tol, stop, rmax, rot);
+            __syncwarp();                  // the norms stored by the pass are read by other lanes next
+          }
+        }
+        if (okA && okB) {
+          for (int k = 0; k < C; ++k) {
+            int a = A * C + sub, b = Bc * C + ((sub + k) & (C - 1));
+            if (a >= p || b >= p) a = b = -1;
+            jacobi_pass<T, TV, L, B>(W, q, ldw, p, V, ldv, nrm, a, b, sl, tol, stop, rmax, rot);
+            __syncwarp();
+          }
+        }
+      }
+      group_sync(bar, nthr);
+    }
     float rm32 = (float)rmax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rm32 = fmaxf(rm32, __shfl_xor_sync(0xffffffffu, rm32, o));
@@ -685,6 +790,9 @@ __device__ __forceinline__ int lanes_per_pair(int q, int p, int nw) {
 template <typename T, typename TV = T, int B = 4>
 __device__ int jacobi_group(T* __restrict__ W, int q, int ldw, int p, TV* __restrict__ V, int ldv,
                             T* __restrict__ nrm, int lw, int nw, int bar, int g, GroupSh& gs, T stop, int max_sweeps) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (p >= 16) return jacobi_blocks<T, TV, B>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
+  }
   const int L = lanes_per_pair(q, p, nw);
   if (L == 8) return jacobi_lanes<T, TV, 8, B>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);
   if (L == 16) return jacobi_lanes<T, TV, 16, B>(W, q, ldw, p, V, ldv, nrm, lw, nw, bar, g, gs, stop, max_sweeps);

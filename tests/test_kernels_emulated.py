@@ -330,3 +330,35 @@ def test_two_chains_per_sm_kernel_matches_the_oracle(emu):
         assert list(env[k]) == r["env_out"]
     obs2, env2, lp2 = run("random:3")
     assert np.array_equal(obs, obs2) and np.array_equal(env, env2) and np.array_equal(lp, lp2)
+
+
+def test_block_ordered_jacobi_matches_the_oracle(emu):
+    """A ladder whose splits have charge blocks of 16 to 19 columns, where the
+    binary32 sweeps take the block ordering (super-columns of four, one group
+    barrier per super-round): one HM_MIXED sample within the binary32 bars of
+    the oracle, the oracle's outcomes, and bit-identical under a shuffled
+    thread order (a race check of the warp-local sub-rounds)."""
+    cfg = dict(Lx=3, two_W=2, J_leg=1.0, J_rung=0.7, beta=0.6, tau=0.1, chi_max=48, cutoff=1e-10)
+
+    def run(order):
+        old = os.environ.get("SIMT_ORDER")
+        os.environ["SIMT_ORDER"] = order
+        try:
+            e = Emu(emu)
+            p = binding.params(**cfg, seed=1, chain_id=2, precision=binding.HM_MIXED)
+            cid = e.init(p)
+            out = e.sample(cid, p)
+            e.close()
+            return out
+        finally:
+            if old is None:
+                os.environ.pop("SIMT_ORDER", None)
+            else:
+                os.environ["SIMT_ORDER"] = old
+    obs, env, lp = run("forward")
+    r = ochain.HybridChain(seed=1, chain_id=2, **cfg).sample()
+    assert abs(obs[0] - r["obs"][0]) < 1e-5 * abs(r["obs"][0])
+    assert np.abs(obs[1:] - r["obs"][1:]).max() < 2e-5
+    assert env == r["env_out"]
+    obs2, env2, lp2 = run("random:5")
+    assert np.array_equal(obs, obs2) and env == env2 and lp == lp2
