@@ -780,6 +780,9 @@ __device__ __forceinline__ int lanes_per_pair(int q, int p, int nw) {
   return best;
 }
 
+// One-sided Jacobi of one block by a warp group: the block ordering
+// (jacobi_blocks) for binary32 blocks of 16 columns or more, otherwise the
+// round-robin ordering with L lanes per pair from the latency model.
 // TV: element type of V.  A binary64 polish of a binary32 result may keep V
 // in binary32: V carries binary32 accuracy from the preconditioning sweeps
 // anyway, and the polish's rotations are tiny (angles ~1e-6).

@@ -10,11 +10,13 @@
 // singular values and the stored site tensors stay binary64.  Measurement
 // and collapse (steps 3-4) are the binary64 kernels of hm_fp64.cu.
 //
-// One CTA owns one chain.  The blocks of a split that fit in shared memory
-// together form a wave and are decomposed at once, each by its own warp
-// group; a block too large for shared memory keeps W and V in global memory
-// and works on pairs of column blocks staged in shared memory (intra-block
-// pairs once per sweep, then every cross pair of two staged blocks).
+// One CTA owns one chain: 512 threads, one CTA per SM, or (hm_mixed_pair.cu)
+// 256 threads, two CTAs per SM, for batches wider than the GPU.  The blocks
+// of a split that fit in shared memory together form a wave and are
+// decomposed at once, each by its own warp group; a block too large for
+// shared memory keeps W and V in global memory and works on pairs of column
+// blocks staged in shared memory (intra-block pairs once per sweep, then
+// every cross pair of two staged blocks).
 #include <cuda_runtime.h>
 
 #include <cfloat>
