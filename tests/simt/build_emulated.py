@@ -18,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_1910_09142_gb300", "csrc")
 KERNELS = ("hm_fp64.cu", "hm_mixed.cu", "hm_mixed_pair.cu")
+# test-only kernel sources (this folder), rewritten the same way
+PROBES = ("jacobi_harness.cu",)
 
 
 def rewrite(text):
@@ -44,9 +46,9 @@ def build(out_dir, cxx=None):
     flags = ["-std=c++20", "-O2", "-fPIC", "-I" + inc, "-I" + CSRC]
     objs = []
     jobs = []
-    for name in KERNELS:
+    for name in KERNELS + PROBES:
         src = os.path.join(out_dir, name.replace(".cu", ".cpp"))
-        with open(os.path.join(CSRC, name)) as f:
+        with open(os.path.join(CSRC if name in KERNELS else HERE, name)) as f:
             text = rewrite(f.read())
         with open(src, "w") as f:
             f.write(text)

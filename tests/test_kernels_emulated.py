@@ -362,3 +362,96 @@ def test_block_ordered_jacobi_matches_the_oracle(emu):
     assert env == r["env_out"]
     obs2, env2, lp2 = run("random:5")
     assert np.array_equal(obs, obs2) and env == env2 and lp == lp2
+
+
+def _graded(q, p, lo, seed):
+    r = np.random.default_rng(seed)
+    U = np.linalg.qr(r.standard_normal((q, p)))[0]
+    Vt = np.linalg.qr(r.standard_normal((p, p)))[0]
+    return U @ np.diag(np.logspace(0, lo, p)) @ Vt
+
+
+def _jacobi_cases():
+    rng = np.random.default_rng(0)
+    noisy = _graded(40, 40, -4, 2)
+    # twenty columns at 1e-19 of the rest, partly along them: the case whose
+    # overlaps a pair-relative size floor once kept from converging
+    noisy[:, 20:] = rng.standard_normal((40, 20)) * 1e-19 + noisy[:, :20] @ rng.standard_normal((20, 20)) * 1e-16
+    q1 = np.linalg.qr(rng.standard_normal((36, 36)))[0]
+    q2 = np.linalg.qr(rng.standard_normal((36, 36)))[0]
+    degenerate = q1 @ np.diag([1.0] * 12 + [0.5] * 12 + [0.25] * 12) @ q2.T   # exact multiplets
+    # three scales: columns of order 1, 1e-4 to 1e-2, and 1e-19 to 1e-17 with
+    # components along the first; a size floor relative to each pair's
+    # larger column (an earlier form of the binary64 tests) never converges
+    # on this one, the per-operand scaling does in ~11 sweeps
+    r = np.random.default_rng(8)
+    big = r.standard_normal((40, 8))
+    mid = r.standard_normal((40, 16)) * 10 ** r.uniform(-4, -2, 16)
+    tiny = (r.standard_normal((40, 16)) + big @ r.standard_normal((8, 16)) * 10 ** r.uniform(0, 3)) * \
+        10 ** r.uniform(-19, -17, 16)
+    three = np.hstack([big, mid, tiny])[:, r.permutation(40)]
+    return {"graded": _graded(40, 24, -12, 1), "noise_columns": noisy, "degenerate": degenerate,
+            "graded_wide": _graded(48, 32, -6, 3), "small": _graded(20, 12, -6, 4), "three_scales": three}
+
+
+@pytest.mark.parametrize("binary64", [True, False])
+@pytest.mark.parametrize("case", ["graded", "noise_columns", "degenerate", "graded_wide", "small", "three_scales"])
+def test_block_jacobi_against_numpy(emu, case, binary64):
+    """jacobi_group on one block (tests/simt/jacobi_harness.cu), the library's
+    Jacobi itself: binary64 with the binary64 kernels' stopping ratio (1e-9),
+    binary32 with the mixed kernel's (2e-4; blocks of 16 columns or more take
+    the block ordering).  Converged within the sweep limit; singular values
+    (the column norms of W) against numpy's SVD; V orthogonal; W = A V; the
+    columns of W orthogonal (relative to their norms, above 1e-12 of the
+    largest).  Bars: binary64 1e-13, binary32 3e-5 (a few ulp of the
+    accumulated rotations)."""
+    emu.hm_probe_jacobi.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double]
+    A = _jacobi_cases()[case]
+    q, p = A.shape
+    dt = np.float64 if binary64 else np.float32
+    W = np.asfortranarray(A.astype(dt))
+    V = np.asfortranarray(np.eye(p, dtype=dt))
+    sweeps = emu.hm_probe_jacobi(W.ctypes.data, q, p, V.ctypes.data, int(binary64), 256, 1e-9 if binary64 else 2e-4)
+    assert 1 <= sweeps <= (20 if case == "three_scales" else 60)
+    W, V = W.astype(np.float64), V.astype(np.float64)
+    bar = 1e-13 if binary64 else 3e-5
+    sv = np.sort(np.linalg.norm(W, axis=0))[::-1]
+    ref = np.linalg.svd(A, compute_uv=False)
+    assert np.abs(sv - ref).max() <= bar * ref[0]
+    assert np.abs(V.T @ V - np.eye(p)).max() <= bar
+    assert np.abs(W - A @ V).max() <= bar * np.abs(A).max()
+    G = W.T @ W
+    d = np.sqrt(np.diag(G))
+    big = d > 1e-12 * d.max()
+    off = np.abs(G - np.diag(np.diag(G)))[np.ix_(big, big)] / np.outer(d[big], d[big])
+    assert off.max() <= bar
+
+
+def test_block_jacobi_is_race_free(emu):
+    """Both orderings and both precisions give bit-identical results whatever
+    order the threads of the block run in."""
+    emu.hm_probe_jacobi.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double]
+    cases = _jacobi_cases()
+
+    def run(A, binary64):
+        dt = np.float64 if binary64 else np.float32
+        W = np.asfortranarray(A.astype(dt))
+        V = np.asfortranarray(np.eye(A.shape[1], dtype=dt))
+        emu.hm_probe_jacobi(W.ctypes.data, A.shape[0], A.shape[1], V.ctypes.data, int(binary64), 128,
+                            1e-9 if binary64 else 2e-4)
+        return W, V
+    old = os.environ.get("SIMT_ORDER")
+    try:
+        for case, binary64 in [("graded_wide", False), ("small", False), ("degenerate", True)]:
+            os.environ["SIMT_ORDER"] = "forward"
+            a = run(cases[case], binary64)
+            os.environ["SIMT_ORDER"] = "random:11"
+            b = run(cases[case], binary64)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), case
+    finally:
+        if old is None:
+            os.environ.pop("SIMT_ORDER", None)
+        else:
+            os.environ["SIMT_ORDER"] = old
