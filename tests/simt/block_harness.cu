@@ -1,7 +1,8 @@
-// TEST INFRASTRUCTURE: runs the library's one-sided Jacobi of one block
-// (hm_block.cuh, jacobi_group) in the CPU emulation, so that the tests can
-// check it directly on crafted matrices (graded spectra, noise-level
-// columns, exact degeneracy) against numpy.  Built only by
+// TEST INFRASTRUCTURE: runs pieces of the library's split (hm_block.cuh) in
+// the CPU emulation, so that the tests can check them directly: the
+// one-sided Jacobi of one block (jacobi_group) on crafted matrices (graded
+// spectra, noise-level columns, exact degeneracy) against numpy, and the
+// truncation rule (trunc_rank) against the oracle's.  Built only by
 // build_emulated.py; the product library never links it.
 #include <vector>
 
@@ -39,4 +40,11 @@ extern "C" int hm_probe_jacobi(void* W, int q, int p, void* V, int binary64, int
     jacobi_probe32<<<1, nthreads, 0, nullptr>>>((float*)W, q, p, (float*)V, nrm.data(), (float)stop, &sweeps);
   }
   return sweeps;
+}
+
+// Kept count of the truncation rule for n descending values s (the
+// device function itself, called on the host in the emulation).  tail and
+// total are outputs (tail: n + 1 doubles).
+extern "C" int hm_probe_trunc(const double* s, int n, int chi_max, double cutoff, double* tail, double* total) {
+  return hm::blk::trunc_rank(s, n, chi_max, cutoff, tail, total);
 }

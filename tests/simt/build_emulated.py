@@ -19,7 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_1910_09142_gb300", "csrc")
 KERNELS = ("hm_fp64.cu", "hm_mixed.cu", "hm_mixed_pair.cu")
 # test-only kernel sources (this folder), rewritten the same way
-PROBES = ("jacobi_harness.cu",)
+PROBES = ("block_harness.cu",)
 
 
 def rewrite(text):

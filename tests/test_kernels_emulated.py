@@ -397,7 +397,7 @@ def _jacobi_cases():
 @pytest.mark.parametrize("binary64", [True, False])
 @pytest.mark.parametrize("case", ["graded", "noise_columns", "degenerate", "graded_wide", "small", "three_scales"])
 def test_block_jacobi_against_numpy(emu, case, binary64):
-    """jacobi_group on one block (tests/simt/jacobi_harness.cu), the library's
+    """jacobi_group on one block (tests/simt/block_harness.cu), the library's
     Jacobi itself: binary64 with the binary64 kernels' stopping ratio (1e-9),
     binary32 with the mixed kernel's (2e-4; blocks of 16 columns or more take
     the block ordering).  Converged within the sweep limit; singular values
@@ -455,3 +455,32 @@ def test_block_jacobi_is_race_free(emu):
             os.environ.pop("SIMT_ORDER", None)
         else:
             os.environ["SIMT_ORDER"] = old
+
+
+def test_truncation_rule_matches_the_oracle(emu):
+    """trunc_rank (the kernels' kept count) against the oracle's rule on the
+    same descending values, bit for bit: random spectra over the cutoff and
+    chi-cap boundaries, exact multiplets that the tie rule must not split,
+    near-ties either side of the 1e-8 relative gap, a single value, and the
+    discarded weight landing exactly on the cutoff."""
+    from oracle import mps as omps
+    emu.hm_probe_trunc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                   ctypes.c_void_p]
+    rng = np.random.default_rng(21)
+    cases = []
+    for _ in range(200):
+        n = int(rng.integers(1, 120))
+        s = np.sort(np.exp(rng.uniform(-12, 0, n)))[::-1]
+        cases.append((s, int(rng.integers(1, 130)), float(10 ** rng.uniform(-14, -2))))
+    mult = np.repeat([1.0, 0.3, 0.3 * (1 - 5e-9), 0.1, 1e-3], [1, 3, 2, 5, 3])     # a multiplet split by < 1e-8
+    for chi in range(1, len(mult) + 1):
+        cases.append((np.sort(mult)[::-1], chi, 1e-12))
+    near = np.array([1.0, 0.5, 0.5 * (1 - 2e-8), 0.25])                        # a gap just above 1e-8
+    cases += [(near, 2, 1e-14), (near, 3, 1e-14), (np.array([0.7]), 4, 1e-7)]
+    w = np.array([0.8, 0.6]) ** 2
+    cases.append((np.array([0.8, 0.6]), 2, float(w[1] / w.sum())))               # weight exactly at the cutoff
+    for s, chi, cut in cases:
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        tail, total = np.zeros(len(s) + 1), np.zeros(1)
+        k = emu.hm_probe_trunc(s.ctypes.data, len(s), chi, cut, tail.ctypes.data, total.ctypes.data)
+        assert k == omps.truncation_rank(s, chi, cut), (len(s), chi, cut)
